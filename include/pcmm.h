@@ -1,0 +1,181 @@
+/*
+ * pcmm.h - C ABI of libpcmm: plaintext-ciphertext matrix multiplication
+ * (PC-MM) with EC-ElGamal over NIST P-256 on one GB300 GPU (sm_103a).
+ *
+ * Method: arXiv 2504.14497.  A plaintext matrix A (m x n, entries below 2^w)
+ * multiplies an element-wise encrypted matrix Enc(B) (n x l), each ciphertext
+ * being the pair of curve points (C1, C2) = (rG, rH + bG) (Section 2.4).  The
+ * result is Enc(A B): C_ij = sum_k a_ik Enc(b_kj) as point sums
+ * (Section 3.1; Eq. ahe_5_elgamal).
+ *
+ * ---------------------------------------------------------------------------
+ * Conventions
+ * ---------------------------------------------------------------------------
+ * Field elements: 8 x uint32 little-endian limbs, value below p
+ *   (p = 2^256 - 2^224 + 2^192 + 2^96 - 1, Section 4.1).
+ *
+ * Point arrays in device memory are QUAD-PLANAR: for an array of N points,
+ *   coordinate quad q (limbs 4q'..4q'+3 of one coordinate) of point i is the
+ *   16-byte word at uint32 offset 4 * (q * N + i).
+ *   Affine points: 4 quads per point = x[0..3], x[4..7], y[0..3], y[4..7];
+ *     infinity is x = y = 0 (not on the curve since b != 0).
+ *   Jacobian points (x = X/Z^2, y = Y/Z^3): 6 quads = X lo/hi, Y lo/hi,
+ *     Z lo/hi; infinity has Z = 0.
+ * Ciphertext arrays of `count` elements are two point arrays, C1 then C2:
+ *   affine  : PCMM_AFF_WORDS  = 32 uint32 words per ciphertext,
+ *             C1 quads at uint32 offset 0, C2 quads at offset 16 * count;
+ *   Jacobian: PCMM_JAC_WORDS  = 48 words per ciphertext,
+ *             C1 at offset 0, C2 at offset 24 * count.
+ * A matrix of ciphertexts with R rows and L columns is such an array with
+ *   count = R * L and element (r, c) at index r * L + c.
+ * Scalars (encryption nonces r): quad-planar with 2 quads per scalar
+ *   (limbs 0..3, limbs 4..7), 8 words per scalar.
+ * The plaintext matrix A: device uint8, row-major m x n, entries < 2^w.
+ *
+ * Every compute call is asynchronous on the caller's CUDA stream (NULL means
+ * the legacy default stream) and allocates no memory: the caller owns all
+ * buffers, including the workspace.  Pointers documented as "device" must
+ * point to device (or managed) memory of the current device; "host" means
+ * host memory.  Argument errors are detected before any launch and return
+ * PCMM_EINVAL with nothing enqueued; a failed launch returns PCMM_ECUDA.
+ */
+#ifndef PCMM_H_
+#define PCMM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *pcmm_stream_t; /* a cudaStream_t */
+
+typedef enum {
+    PCMM_OK = 0,
+    PCMM_EINVAL = 1,       /* bad argument (sizes, widths, null pointers)     */
+    PCMM_ENOMEM = 2,       /* workspace smaller than required                 */
+    PCMM_ECUDA = 3,        /* a CUDA call or kernel launch failed             */
+    PCMM_ETIMEOUT = 4,     /* a bounded device-side wait gave up              */
+    PCMM_EUNSUPPORTED = 5, /* valid request outside what this build supports */
+    PCMM_EDEVICE = 6       /* a kernel flagged bad data (see workspace status) */
+} pcmm_status;
+
+#define PCMM_AFF_WORDS 32
+#define PCMM_JAC_WORDS 48
+#define PCMM_MAX_W 8      /* plaintext bit-width w of A: 1..8 */
+#define PCMM_MAX_WK 12    /* strip code width w * k is at most 12 bits */
+#define PCMM_N_ITER 4     /* Cussen compression iterations N (Section 3.2) */
+
+/* Library ABI version (major * 10000 + minor * 100 + patch). */
+int pcmm_version(void);
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *pcmm_status_string(int status);
+
+/* Builds the fixed-base table of the generator G in static device memory of
+ * `device` (makes it current).  Idempotent and cheap after the first call;
+ * synchronous.  Must precede pcmm_encrypt on that device.
+ * Errors: PCMM_ECUDA if the device cannot be used. */
+pcmm_status pcmm_init(int device);
+
+/* ------------------------------------------------------------------------
+ * Encryption (Section 2.4): Enc(b) = (rG, rH + bG), phi(b) = bG.
+ * Fixed-base comb with one table per 8-bit window: for a base point X,
+ * T[i][v] = v 2^(8i) X, i = 0..31, v = 0..255, so that
+ * rX = sum_i T[i][byte_i(r)] costs at most 32 mixed additions.
+ * ---------------------------------------------------------------------- */
+
+/* Bytes of one key table (the comb table of H). */
+size_t pcmm_keytable_bytes(void);
+
+/* Builds the comb table of the public key H.
+ * H_host: host, 16 words (x then y), canonical, on the curve, not infinity.
+ * keytable: device, pcmm_keytable_bytes() bytes, 16-byte aligned; written.
+ * Errors: PCMM_EINVAL (null pointer, H not reduced or infinity). */
+pcmm_status pcmm_keytable(const uint32_t *H_host, void *keytable, pcmm_stream_t stream);
+
+/* Encrypts count messages.
+ * keytable: device, from pcmm_keytable (read only).
+ * msg: device uint8[count].  r: device scalars (quad-planar, 8 * count
+ * words); each r is used modulo q (Section 2.4 draws r from [1, q-1]).
+ * ct: device, affine ciphertext array of count elements (32 * count words),
+ * written canonical.  Requires pcmm_init on the current device.
+ * Errors: PCMM_EINVAL (null pointers), PCMM_ECUDA. */
+pcmm_status pcmm_encrypt(const void *keytable, const uint8_t *msg, const uint32_t *r, size_t count,
+                         uint32_t *ct, pcmm_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * PC-MM.  Inputs: A (device uint8 m x n, entries < 2^w), ctB (device affine
+ * ciphertext matrix n x l).  Output: ctC (device Jacobian ciphertext matrix
+ * m x l, 48 * m * l words), C_ij = sum_k a_ik (B1_kj, B2_kj).
+ * ctC must not overlap the inputs.  m, n, l >= 1; 1 <= w <= 8.
+ * ---------------------------------------------------------------------- */
+
+/* Schoolbook PC-MM (Section 3.1): every product a_ik B^(kj) by left-to-right
+ * double-and-add over the bits of a_ik, then accumulated by point additions.
+ * Needs no workspace.  Errors: PCMM_EINVAL, PCMM_ECUDA. */
+pcmm_status pcmm_schoolbook(const uint8_t *A, int m, int n, int w, const uint32_t *ctB, int l,
+                            uint32_t *ctC, pcmm_stream_t stream);
+
+/* Strip width chosen by the built-in cost model for a problem shape: the k
+ * in [1, 12/w] minimising the modelled point-addition work (table build,
+ * normalisation and gather). */
+int pcmm_cussen_choose_k(int m, int n, int l, int w);
+
+/* Workspace bytes pcmm_cussen needs for this shape and strip width k
+ * (k = 0: the pcmm_cussen_choose_k value).  Returns 0 for invalid
+ * arguments.  Larger workspaces let a call process more strips per pass. */
+size_t pcmm_cussen_workspace_bytes(int m, int n, int l, int w, int k);
+
+/* Cussen PC-MM (Algorithms 2 and 3).  Strip width k = 1 is Algorithm 3 as
+ * printed: each column of A is compressed (sort, remove duplicates, take
+ * differences; N = 4 iterations), the compressed values are multiplied by
+ * each ciphertext of that row of Enc(B), reconstruction by prefix sums of
+ * points rebuilds the multiples of every distinct value, and each output
+ * ciphertext adds the multiple its entry selects (the un-sort step fused
+ * with the accumulation).  k > 1 (an extension, not in the paper) also
+ * combines k adjacent columns into one table of the distinct k-tuples of
+ * the strip, so the gather adds once per strip instead of once per column.
+ * The result is identical for every k.
+ * k: 1 <= k <= 12 / w, or 0 for pcmm_cussen_choose_k.
+ * ws: device workspace, 256-byte aligned, of at least
+ * pcmm_cussen_workspace_bytes(m, n, l, w, k) bytes; its first 4 bytes are a
+ * status word that kernels OR error bits into (1: an entry of A >= 2^w,
+ * such entries are masked to w bits).  The status word is cleared at the
+ * start of every call; read it with pcmm_workspace_status.
+ * Errors: PCMM_EINVAL, PCMM_ENOMEM (workspace too small), PCMM_ECUDA. */
+pcmm_status pcmm_cussen(const uint8_t *A, int m, int n, int w, const uint32_t *ctB, int l,
+                        uint32_t *ctC, int k, void *ws, size_t ws_bytes, pcmm_stream_t stream);
+
+/* Reads the status word of a pcmm_cussen workspace into *status_host after
+ * synchronising `stream`.  0 means no kernel raised an error bit. */
+pcmm_status pcmm_workspace_status(const void *ws, uint32_t *status_host, pcmm_stream_t stream);
+
+/* Normalises a Jacobian ciphertext array to canonical affine form
+ * (Montgomery's simultaneous inversion, one field inversion per 64 points).
+ * ct_jac: device, 48 * count words; ct_aff: device, 32 * count words
+ * (may not overlap).  Errors: PCMM_EINVAL, PCMM_ECUDA. */
+pcmm_status pcmm_normalize(const uint32_t *ct_jac, size_t count, uint32_t *ct_aff,
+                           pcmm_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Unit-test entry points for the device arithmetic (device arrays of
+ * `count` items, quad-planar like the point arrays).
+ * pcmm_test_field: op 0 add, 1 sub, 2 mul, 3 sqr, 4 inv, 5 canonical
+ *   form; a, b: 2 quads per element (b unused for ops 3-5); out canonical.
+ * pcmm_test_point: op 0 dbl(P), 1 P + Q (mixed: Q affine), 2 P + Q (both
+ *   Jacobian), 3 k P for a small scalar k (P affine, k = kscal[i]);
+ *   P: Jacobian (6 quads) for ops 0-2, affine (4 quads) for op 3; Q: affine
+ *   (op 1) or Jacobian (op 2); out: affine canonical (4 quads).
+ * ---------------------------------------------------------------------- */
+pcmm_status pcmm_test_field(int op, const uint32_t *a, const uint32_t *b, uint32_t *out,
+                            size_t count, pcmm_stream_t stream);
+pcmm_status pcmm_test_point(int op, const uint32_t *P, const uint32_t *Q, const uint32_t *kscal,
+                            uint32_t *out, size_t count, pcmm_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCMM_H_ */

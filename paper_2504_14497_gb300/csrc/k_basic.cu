@@ -1,0 +1,269 @@
+// Encryption (Section 2.4), output normalisation, and unit-test entry points
+// for the device field and group arithmetic.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+using namespace pcmm;
+
+namespace {
+
+constexpr int COMB_WINDOWS = 32;    // 8-bit windows of a 256-bit scalar
+constexpr int COMB_ENTRIES = 256;   // v = 0..255 per window (v = 0 unused)
+constexpr int COMB_POINTS = COMB_WINDOWS * COMB_ENTRIES;
+
+// Comb table of the generator, quad-planar with stride COMB_POINTS.
+__device__ uint4 g_comb_G[4 * COMB_POINTS];
+
+// P-256 generator (SEC 2 / FIPS 186-4), little-endian 32-bit words.
+const uint32_t h_G[16] = {
+    0xd898c296u, 0xf4a13945u, 0x2deb33a0u, 0x77037d81u, 0x63a440f2u, 0xf8bce6e5u, 0xe12c4247u, 0x6b17d1f2u,
+    0x37bf51f5u, 0xcbb64068u, 0x6b315eceu, 0x2bce3357u, 0x7c0f9e16u, 0x8ee7eb4au, 0xfe1a7f9bu, 0x4fe342e2u};
+
+// R <- s P for a 256-bit scalar s (8 little-endian words) by left-to-right
+// double-and-add with mixed additions of the affine P.
+__device__ void jac_mul_u256(jac& R, const aff& P, const uint32_t s[8]) {
+    jac_set_inf(R);
+    bool started = false;
+    for (int b = 255; b >= 0; b--) {
+        if (started) jac_dbl(R);
+        if ((s[b >> 5] >> (b & 31)) & 1u) {
+            jac_madd(R, P);
+            started = true;
+        }
+    }
+}
+
+// Entry (window i, value v) = (v 2^(8i)) X.  One thread per entry; the
+// results are normalised one warp at a time.
+__global__ void __launch_bounds__(128) comb_build_kernel(aff base, uint4* __restrict__ tab) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;  // < COMB_POINTS
+    const int win = idx / COMB_ENTRIES, v = idx % COMB_ENTRIES;
+    uint32_t s[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) s[i] = 0;
+    s[win >> 2] = (uint32_t)v << (8 * (win & 3));
+    jac R[1];
+    jac_mul_u256(R[0], base, s);
+    aff out[1];
+    warp_normalize_regs<1>(out, R);
+    store_aff(tab, COMB_POINTS, idx, out[0]);
+}
+
+// Enc(b) = (rG, rH + bG): 32 window lookups per base point.
+__global__ void __launch_bounds__(128) encrypt_kernel(const uint4* __restrict__ gtab,
+                                                      const uint4* __restrict__ htab,
+                                                      const uint8_t* __restrict__ msg,
+                                                      const uint4* __restrict__ r, size_t count,
+                                                      uint4* __restrict__ ct) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < count;
+    const size_t ii = valid ? i : 0;
+    fe rr;
+    fe_from_quads(rr, r[ii], r[count + ii]);
+    jac P[2];
+    jac_set_inf(P[0]);
+    jac_set_inf(P[1]);
+    aff T;
+    for (int win = 0; win < COMB_WINDOWS; win++) {
+        const uint32_t v = (rr.v[win >> 2] >> (8 * (win & 3))) & 0xffu;
+        if (v) {
+            load_aff(T, gtab, COMB_POINTS, (size_t)win * COMB_ENTRIES + v);
+            jac_madd(P[0], T);
+            load_aff(T, htab, COMB_POINTS, (size_t)win * COMB_ENTRIES + v);
+            jac_madd(P[1], T);
+        }
+    }
+    const uint32_t b = msg[ii];
+    if (b) {
+        load_aff(T, gtab, COMB_POINTS, b);
+        jac_madd(P[1], T);
+    }
+    aff out[2];
+    warp_normalize_regs<2>(out, P);
+    if (valid) {
+        store_aff(ct, count, i, out[0]);
+        store_aff(ct + 4 * count, count, i, out[1]);
+    }
+}
+
+// Jacobian ciphertexts -> canonical affine, one thread per ciphertext.
+__global__ void __launch_bounds__(128) normalize_kernel(const uint4* __restrict__ in, size_t count,
+                                                        uint4* __restrict__ out) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < count;
+    const size_t ii = valid ? i : 0;
+    jac P[2];
+    load_jac(P[0], in, count, ii);
+    load_jac(P[1], in + 6 * count, count, ii);
+    aff A[2];
+    warp_normalize_regs<2>(A, P);
+    if (valid) {
+        store_aff(out, count, i, A[0]);
+        store_aff(out + 4 * count, count, i, A[1]);
+    }
+}
+
+__global__ void __launch_bounds__(128) test_field_kernel(int op, const uint4* __restrict__ a,
+                                                         const uint4* __restrict__ b,
+                                                         uint4* __restrict__ out, size_t count) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    fe x, y, r;
+    load_fe(x, a, count, i);
+    if (op <= 2) load_fe(y, b, count, i);
+    switch (op) {
+        case 0: fe_add(r, x, y); break;
+        case 1: fe_sub(r, x, y); break;
+        case 2: fe_mul(r, x, y); break;
+        case 3: fe_sqr(r, x); break;
+        case 4: fe_inv(r, x); break;
+        default: r = x; break;
+    }
+    fe_canon(r, r);
+    store_fe(out, count, i, r);
+}
+
+__global__ void __launch_bounds__(128) test_point_kernel(int op, const uint4* __restrict__ P,
+                                                         const uint4* __restrict__ Q,
+                                                         const uint32_t* __restrict__ ks,
+                                                         uint4* __restrict__ out, size_t count) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < count;
+    const size_t ii = valid ? i : 0;
+    jac R[1];
+    if (op == 3) {
+        aff A;
+        load_aff(A, P, count, ii);
+        jac_mul_small(R[0], A, ks[ii]);
+    } else {
+        load_jac(R[0], P, count, ii);
+        if (op == 0) {
+            jac_dbl(R[0]);
+        } else if (op == 1) {
+            aff B;
+            load_aff(B, Q, count, ii);
+            jac_madd(R[0], B);
+        } else {
+            jac B;
+            load_jac(B, Q, count, ii);
+            jac_add(R[0], B);
+        }
+    }
+    aff o[1];
+    warp_normalize_regs<1>(o, R);
+    if (valid) store_aff(out, count, i, o[0]);
+}
+
+inline unsigned grid_for(size_t count, unsigned block) { return (unsigned)((count + block - 1) / block); }
+
+bool g_ready[64] = {false};
+
+}  // namespace
+
+extern "C" int pcmm_version(void) { return 10000; }
+
+extern "C" const char* pcmm_status_string(int s) {
+    switch (s) {
+        case PCMM_OK: return "PCMM_OK";
+        case PCMM_EINVAL: return "PCMM_EINVAL: invalid argument";
+        case PCMM_ENOMEM: return "PCMM_ENOMEM: workspace too small";
+        case PCMM_ECUDA: return "PCMM_ECUDA: CUDA error";
+        case PCMM_ETIMEOUT: return "PCMM_ETIMEOUT: device wait timed out";
+        case PCMM_EUNSUPPORTED: return "PCMM_EUNSUPPORTED: unsupported request";
+        case PCMM_EDEVICE: return "PCMM_EDEVICE: a kernel flagged invalid data";
+        default: return "unknown pcmm status";
+    }
+}
+
+extern "C" pcmm_status pcmm_init(int device) {
+    if (device < 0 || device >= 64) return PCMM_EINVAL;
+    if (cudaSetDevice(device) != cudaSuccess) return PCMM_ECUDA;
+    if (g_ready[device]) return PCMM_OK;
+    aff G;
+    for (int i = 0; i < 8; i++) {
+        G.x.v[i] = h_G[i];
+        G.y.v[i] = h_G[8 + i];
+    }
+    uint4* tab = nullptr;
+    if (cudaGetSymbolAddress((void**)&tab, g_comb_G) != cudaSuccess) return PCMM_ECUDA;
+    comb_build_kernel<<<COMB_POINTS / 128, 128>>>(G, tab);
+    PCMM_CUDA_CHECK_LAUNCH();
+    if (cudaDeviceSynchronize() != cudaSuccess) return PCMM_ECUDA;
+    g_ready[device] = true;
+    return PCMM_OK;
+}
+
+extern "C" size_t pcmm_keytable_bytes(void) { return (size_t)COMB_POINTS * 64; }
+
+static bool reduced_below_p(const uint32_t* v) {
+    static const uint32_t p[8] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u, 1u, 0xffffffffu};
+    for (int i = 7; i >= 0; i--) {
+        if (v[i] < p[i]) return true;
+        if (v[i] > p[i]) return false;
+    }
+    return false;
+}
+
+extern "C" pcmm_status pcmm_keytable(const uint32_t* H_host, void* keytable, pcmm_stream_t stream) {
+    if (!H_host || !keytable || ((uintptr_t)keytable & 15u)) return PCMM_EINVAL;
+    if (!reduced_below_p(H_host) || !reduced_below_p(H_host + 8)) return PCMM_EINVAL;
+    aff H;
+    uint32_t z = 0;
+    for (int i = 0; i < 8; i++) {
+        H.x.v[i] = H_host[i];
+        H.y.v[i] = H_host[8 + i];
+        z |= H_host[i] | H_host[8 + i];
+    }
+    if (!z) return PCMM_EINVAL;
+    comb_build_kernel<<<COMB_POINTS / 128, 128, 0, (cudaStream_t)stream>>>(H, (uint4*)keytable);
+    PCMM_CUDA_CHECK_LAUNCH();
+    return PCMM_OK;
+}
+
+extern "C" pcmm_status pcmm_encrypt(const void* keytable, const uint8_t* msg, const uint32_t* r,
+                                    size_t count, uint32_t* ct, pcmm_stream_t stream) {
+    if (!keytable || !msg || !r || !ct) return PCMM_EINVAL;
+    if (count == 0) return PCMM_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PCMM_ECUDA;
+    if (dev < 0 || dev >= 64 || !g_ready[dev]) return PCMM_EINVAL;
+    uint4* gtab = nullptr;
+    if (cudaGetSymbolAddress((void**)&gtab, g_comb_G) != cudaSuccess) return PCMM_ECUDA;
+    encrypt_kernel<<<grid_for(count, 128), 128, 0, (cudaStream_t)stream>>>(
+        gtab, (const uint4*)keytable, msg, (const uint4*)r, count, (uint4*)ct);
+    PCMM_CUDA_CHECK_LAUNCH();
+    return PCMM_OK;
+}
+
+extern "C" pcmm_status pcmm_normalize(const uint32_t* ct_jac, size_t count, uint32_t* ct_aff,
+                                      pcmm_stream_t stream) {
+    if (!ct_jac || !ct_aff) return PCMM_EINVAL;
+    if (count == 0) return PCMM_OK;
+    normalize_kernel<<<grid_for(count, 128), 128, 0, (cudaStream_t)stream>>>(
+        (const uint4*)ct_jac, count, (uint4*)ct_aff);
+    PCMM_CUDA_CHECK_LAUNCH();
+    return PCMM_OK;
+}
+
+extern "C" pcmm_status pcmm_test_field(int op, const uint32_t* a, const uint32_t* b, uint32_t* out,
+                                       size_t count, pcmm_stream_t stream) {
+    if (op < 0 || op > 5 || !a || !out || (op <= 2 && !b)) return PCMM_EINVAL;
+    if (count == 0) return PCMM_OK;
+    test_field_kernel<<<grid_for(count, 128), 128, 0, (cudaStream_t)stream>>>(
+        op, (const uint4*)a, (const uint4*)b, (uint4*)out, count);
+    PCMM_CUDA_CHECK_LAUNCH();
+    return PCMM_OK;
+}
+
+extern "C" pcmm_status pcmm_test_point(int op, const uint32_t* P, const uint32_t* Q,
+                                       const uint32_t* kscal, uint32_t* out, size_t count,
+                                       pcmm_stream_t stream) {
+    if (op < 0 || op > 3 || !P || !out || ((op == 1 || op == 2) && !Q) || (op == 3 && !kscal))
+        return PCMM_EINVAL;
+    if (count == 0) return PCMM_OK;
+    test_point_kernel<<<grid_for(count, 128), 128, 0, (cudaStream_t)stream>>>(
+        op, (const uint4*)P, (const uint4*)Q, kscal, (uint4*)out, count);
+    PCMM_CUDA_CHECK_LAUNCH();
+    return PCMM_OK;
+}

@@ -1,0 +1,526 @@
+// Cussen's compression-reconstruction PC-MM (Algorithms 2 and 3) on sm_103a.
+//
+// Three kernels per pass over a chunk of column strips of A:
+//
+//  plan   (once per call, one CTA per strip; plaintext only)
+//         For every column: level 1 = the distinct non-zero values sorted
+//         ascending; for w < N its consecutive differences are sorted and
+//         deduplicated into level w + 1, recording for every element of
+//         level w its position in level w + 1 (the tracking pointers);
+//         level N keeps its values.  A zero contributes the identity and is
+//         dropped from every level.  For the strip: the code of every row
+//         (its k entries packed w bits apiece), the sorted list of distinct
+//         non-zero codes, and each row's rank in that list (0xFFFF for 0).
+//  table  (one warp per strip, ciphertext component and 32 output columns)
+//         Level N: the compressed values times the ciphertext point B_c^(kj)
+//         by double-and-add (the ECSMs of Algorithm 3).  Levels N-1..1: each
+//         element of level w is the entry of level w + 1 its tracking pointer
+//         names, and a running prefix sum of points turns the multiples of
+//         differences into the multiples of the level's sorted values.
+//         Level 1 is the per-column table v B_c^(kj) over the distinct values
+//         v of the column.  For strips of k > 1 columns, each distinct k-tuple
+//         adds its columns' entries.  The table is then normalised to affine
+//         coordinates in the same kernel (Montgomery's simultaneous inversion:
+//         per-lane prefix products, then warp-shuffle prefix products and one
+//         inversion per warp).
+//  gather (one warp per output row i, component c and 32 output columns)
+//         C_ij += T_s[rank_s(i)] for every strip s: the "un-sort and re-insert
+//         duplicates" step of Algorithm 2 fused with the accumulation of
+//         Algorithm 3, one mixed addition per strip.  The rank is the same for
+//         the whole warp (one broadcast load); the 32 lanes' table entries are
+//         adjacent, so the four 16-byte loads per point are coalesced.
+#include <cuda_runtime.h>
+
+#include <math.h>
+
+#include "common.cuh"
+
+using namespace pcmm;
+
+namespace {
+
+constexpr int NLEV = PCMM_N_ITER;   // compression iterations N
+constexpr uint16_t NO_RANK = 0xFFFFu;
+constexpr int PLAN_THREADS = 256;
+
+struct Layout {
+    int m, n, l, w, k;
+    int nstrips, n1max, l2max, emax, lp, njb;
+    size_t off_rank, off_nent, off_codes, off_len, off_vN, off_ptr, off_rank1, plan_bytes;
+    size_t item_u4, items_per_strip, table_points_per_strip, per_strip_bytes;
+};
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Largest d with d (d + 1) / 2 <= 2^w - 1: the distinct positive differences
+// of distinct values below 2^w sum to at most 2^w - 1, so every level after
+// the first holds at most d entries.
+inline int level2_bound(int w) {
+    int lim = (1 << w) - 1, d = 0;
+    while ((d + 1) * (d + 2) / 2 <= lim) d++;
+    return d < 1 ? 1 : d;
+}
+
+bool make_layout(Layout& L, int m, int n, int l, int w, int k) {
+    if (m < 1 || n < 1 || l < 1 || w < 1 || w > PCMM_MAX_W || k < 1 || w * k > PCMM_MAX_WK) return false;
+    L.m = m; L.n = n; L.l = l; L.w = w; L.k = k;
+    L.nstrips = (n + k - 1) / k;
+    L.n1max = (1 << w) - 1 < m ? (1 << w) - 1 : m;
+    L.l2max = level2_bound(w);
+    L.emax = (1 << (w * k)) - 1 < m ? (1 << (w * k)) - 1 : m;
+    L.njb = (l + 31) / 32;
+    L.lp = L.njb * 32;
+    size_t off = 256;  // status word and padding
+    L.off_rank = off;  off = align256(off + (size_t)L.nstrips * m * 2);
+    L.off_nent = off;  off = align256(off + (size_t)L.nstrips * 4);
+    L.off_codes = off; off = align256(off + (size_t)L.nstrips * L.emax * 2);
+    L.off_len = off;   off = align256(off + (size_t)n * NLEV * 2);
+    L.off_vN = off;    off = align256(off + (size_t)n * 256);
+    L.off_ptr = off;   off = align256(off + (size_t)n * (NLEV > 1 ? NLEV - 1 : 1) * 256);
+    L.off_rank1 = off; off = align256(off + (size_t)n * 256);
+    L.plan_bytes = off;
+    const size_t ent_jac = (size_t)k * L.n1max + 2 * (size_t)L.l2max + (k > 1 ? (size_t)L.emax : 0);
+    L.item_u4 = ent_jac * 6 * 32 + (size_t)L.emax * 2 * 32;
+    L.items_per_strip = 2 * (size_t)L.njb;
+    L.table_points_per_strip = (size_t)L.emax * 2 * L.lp;
+    L.per_strip_bytes = L.items_per_strip * L.item_u4 * 16 + align256(L.table_points_per_strip * 64);
+    return true;
+}
+
+struct PlanPtrs {
+    uint32_t* status;
+    uint16_t* rank;
+    int32_t* nent;
+    uint16_t* codes;
+    uint16_t* col_len;
+    uint8_t* col_vN;
+    uint8_t* col_ptr;
+    uint8_t* col_rank1;
+};
+
+PlanPtrs plan_ptrs(const Layout& L, void* ws) {
+    uint8_t* b = (uint8_t*)ws;
+    PlanPtrs P;
+    P.status = (uint32_t*)b;
+    P.rank = (uint16_t*)(b + L.off_rank);
+    P.nent = (int32_t*)(b + L.off_nent);
+    P.codes = (uint16_t*)(b + L.off_codes);
+    P.col_len = (uint16_t*)(b + L.off_len);
+    P.col_vN = b + L.off_vN;
+    P.col_ptr = b + L.off_ptr;
+    P.col_rank1 = b + L.off_rank1;
+    return P;
+}
+
+__device__ __forceinline__ int warp_excl_scan(int v, int& total) {
+    const unsigned lane = threadIdx.x & 31u;
+    int incl = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        int o = __shfl_up_sync(0xffffffffu, incl, d);
+        if ((int)lane >= d) incl += o;
+    }
+    total = __shfl_sync(0xffffffffu, incl, 31);
+    return incl - v;
+}
+
+// Sorted list of the values marked in a 256-bit presence map; also a
+// value -> position map.  Each lane owns 8 consecutive values.
+__device__ __forceinline__ int extract_sorted(const uint32_t* bm, uint16_t* out, uint8_t* pos_of) {
+    const unsigned lane = threadIdx.x & 31u;
+    const uint32_t bits8 = (bm[lane >> 2] >> ((lane & 3u) * 8u)) & 0xffu;
+    int total;
+    int pos = warp_excl_scan(__popc(bits8), total);
+    for (int b = 0; b < 8; b++) {
+        if ((bits8 >> b) & 1u) {
+            const int v = (int)lane * 8 + b;
+            out[pos] = (uint16_t)v;
+            pos_of[v] = (uint8_t)pos;
+            pos++;
+        }
+    }
+    __syncwarp();
+    return total;
+}
+
+__global__ void __launch_bounds__(PLAN_THREADS) plan_kernel(const uint8_t* __restrict__ A, int m, int n,
+                                                            int w, int k, int emax, PlanPtrs P) {
+    __shared__ uint32_t spres[128];
+    __shared__ uint32_t spref[128];
+    __shared__ uint32_t wbm[PLAN_THREADS / 32][8];
+    __shared__ uint16_t wlev[PLAN_THREADS / 32][2][256];
+    __shared__ uint8_t wpos[PLAN_THREADS / 32][256];
+    const int s = blockIdx.x;
+    const int c0 = s * k;
+    const int kw = (c0 + k <= n) ? k : n - c0;
+    const uint32_t amask = (1u << w) - 1u;
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+
+    // ---- per-column compression levels (one warp per column) ----
+    for (int t = (int)warp; t < kw; t += PLAN_THREADS / 32) {
+        const int col = c0 + t;
+        uint32_t* bm = wbm[warp];
+        uint8_t* pos = wpos[warp];
+        if (lane < 8) bm[lane] = 0u;
+        __syncwarp();
+        bool bad = false;
+        for (int i = (int)lane; i < m; i += 32) {
+            uint32_t v = A[(size_t)i * n + col];
+            bad |= v > amask;
+            v &= amask;
+            if (v) atomicOr(&bm[v >> 5], 1u << (v & 31u));
+        }
+        if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(P.status, DEV_ERR_A_RANGE);
+        __syncwarp();
+        uint16_t* cur = wlev[warp][0];
+        uint16_t* nxt = wlev[warp][1];
+        int len = extract_sorted(bm, cur, pos);
+        // value -> level-1 position, for the k-tuple assembly
+        for (int v = (int)lane; v < 256; v += 32) {
+            const bool present = v > 0 && ((bm[v >> 5] >> (v & 31)) & 1u);
+            P.col_rank1[(size_t)col * 256 + v] = present ? pos[v] : (uint8_t)0xff;
+        }
+        if (lane == 0) P.col_len[(size_t)col * NLEV] = (uint16_t)len;
+        __syncwarp();
+        for (int lev = 1; lev < NLEV; lev++) {
+            // Differences of consecutive sorted values; level lev + 1 is their
+            // sorted distinct set.
+            if (lane < 8) bm[lane] = 0u;
+            __syncwarp();
+            for (int e = (int)lane; e < len; e += 32) {
+                const int d = (int)cur[e] - (e ? (int)cur[e - 1] : 0);
+                atomicOr(&bm[d >> 5], 1u << (d & 31));
+            }
+            __syncwarp();
+            const int nlen = extract_sorted(bm, nxt, pos);
+            for (int e = (int)lane; e < len; e += 32) {
+                const int d = (int)cur[e] - (e ? (int)cur[e - 1] : 0);
+                P.col_ptr[((size_t)col * (NLEV - 1) + (lev - 1)) * 256 + e] = pos[d];
+            }
+            if (lane == 0) P.col_len[(size_t)col * NLEV + lev] = (uint16_t)nlen;
+            __syncwarp();
+            uint16_t* tmp = cur; cur = nxt; nxt = tmp;
+            len = nlen;
+        }
+        for (int e = (int)lane; e < len; e += 32) P.col_vN[(size_t)col * 256 + e] = (uint8_t)cur[e];
+        __syncwarp();
+    }
+
+    // ---- strip codes, distinct codes and per-row ranks (whole block) ----
+    for (int x = threadIdx.x; x < 128; x += blockDim.x) spres[x] = 0u;
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        uint32_t code = 0;
+        for (int t = 0; t < kw; t++) code |= ((uint32_t)A[(size_t)i * n + c0 + t] & amask) << (w * t);
+        if (code) atomicOr(&spres[code >> 5], 1u << (code & 31u));
+    }
+    __syncthreads();
+    if (warp == 0) {
+        int cnt = 0;
+        for (int q = 0; q < 4; q++) cnt += __popc(spres[lane * 4 + q]);
+        int total;
+        int base = warp_excl_scan(cnt, total);
+        for (int q = 0; q < 4; q++) {
+            spref[lane * 4 + q] = (uint32_t)base;
+            base += __popc(spres[lane * 4 + q]);
+        }
+        if (lane == 0) P.nent[s] = total;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        uint32_t code = 0;
+        for (int t = 0; t < kw; t++) code |= ((uint32_t)A[(size_t)i * n + c0 + t] & amask) << (w * t);
+        uint16_t r = NO_RANK;
+        if (code) r = (uint16_t)(spref[code >> 5] + __popc(spres[code >> 5] & ((1u << (code & 31u)) - 1u)));
+        P.rank[(size_t)s * m + i] = r;
+    }
+    if (k > 1) {
+        for (int wd = threadIdx.x; wd < 128; wd += blockDim.x) {
+            uint32_t bits = spres[wd];
+            uint32_t r = spref[wd];
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                if ((int)r < emax) P.codes[(size_t)s * emax + r] = (uint16_t)(wd * 32 + b);
+                r++;
+                bits &= bits - 1u;
+            }
+        }
+    }
+}
+
+struct TableArgs {
+    const uint4* ctB;      // affine ciphertext matrix n x l
+    const uint8_t* A;
+    int m, n, l, w, k, lp, njb, n1max, l2max, emax;
+    int s0, nstrips_chunk;
+    uint4* scratch;        // lane-planar per-item scratch
+    size_t item_u4;
+    uint4* table;          // affine, quad-planar, table_points points
+    size_t table_points;
+};
+
+__global__ void __launch_bounds__(128) table_kernel(TableArgs a, PlanPtrs P) {
+    const unsigned lane = threadIdx.x & 31u;
+    const long long item = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nitems = (long long)a.nstrips_chunk * 2 * a.njb;
+    if (item >= nitems) return;
+    const int s_local = (int)(item / (2 * a.njb));
+    const int rem = (int)(item % (2 * a.njb));
+    const int c = rem / a.njb, jb = rem % a.njb;
+    const int s = a.s0 + s_local;
+    const int c0 = s * a.k;
+    const int kw = (c0 + a.k <= a.n) ? a.k : a.n - c0;
+    const int j = jb * 32 + (int)lane;
+    const int jj = j < a.l ? j : a.l - 1;
+    const size_t nl = (size_t)a.n * a.l;
+    const uint4* Bc = a.ctB + (size_t)c * 4 * nl;
+    const uint32_t amask = (1u << a.w) - 1u;
+
+    uint4* base = a.scratch + (size_t)item * a.item_u4;
+    uint4* coltab = base;
+    uint4* levA = coltab + (size_t)a.k * a.n1max * 192;
+    uint4* levB = levA + (size_t)a.l2max * 192;
+    uint4* ents_x = levB + (size_t)a.l2max * 192;
+    uint4* pref = ents_x + (a.k > 1 ? (size_t)a.emax * 192 : 0);
+
+    const int E = P.nent[s];
+    bool bad = false;
+
+    for (int t = 0; t < kw; t++) {
+        const int col = c0 + t;
+        uint4* ct_t = coltab + (size_t)t * a.n1max * 192;
+        aff Pb;
+        load_aff(Pb, Bc, nl, (size_t)col * a.l + jj);
+        int lens[NLEV];
+#pragma unroll
+        for (int q = 0; q < NLEV; q++) lens[q] = P.col_len[(size_t)col * NLEV + q];
+        bad |= lens[0] > a.n1max;
+#pragma unroll
+        for (int q = 1; q < NLEV; q++) bad |= lens[q] > a.l2max;
+        if (bad) break;
+        // Level N: multiples of the compressed values (double-and-add).
+        uint4* src = (NLEV == 1) ? ct_t : levA;
+        for (int e = 0; e < lens[NLEV - 1]; e++) {
+            jac T;
+            jac_mul_small(T, Pb, P.col_vN[(size_t)col * 256 + e]);
+            lp_store_jac(src, e, lane, T);
+        }
+        uint4* alt = levB;
+        // Levels N-1..1: un-sort by the tracking pointers, then prefix sums.
+        for (int lev = NLEV - 1; lev >= 1; lev--) {
+            uint4* dst = (lev == 1) ? ct_t : alt;
+            const uint8_t* ptr = P.col_ptr + ((size_t)col * (NLEV - 1) + (lev - 1)) * 256;
+            jac acc, D;
+            jac_set_inf(acc);
+            for (int e = 0; e < lens[lev - 1]; e++) {
+                lp_load_jac(D, src, ptr[e], lane);
+                jac_add(acc, D);
+                lp_store_jac(dst, e, lane, acc);
+            }
+            alt = src;
+            src = dst;
+        }
+    }
+    if (bad) {
+        if (lane == 0) atomicOr(P.status, DEV_ERR_PLAN);
+        return;
+    }
+
+    // Entries of the strip table (Jacobian).
+    uint4* ents = coltab;
+    if (a.k > 1) {
+        ents = ents_x;
+        for (int e = 0; e < E; e++) {
+            const uint32_t code = P.codes[(size_t)s * a.emax + e];
+            jac acc, D;
+            jac_set_inf(acc);
+            for (int t = 0; t < kw; t++) {
+                const uint32_t v = (code >> (a.w * t)) & amask;
+                if (v) {
+                    const int r1 = P.col_rank1[(size_t)(c0 + t) * 256 + v];
+                    lp_load_jac(D, coltab + (size_t)t * a.n1max * 192, r1, lane);
+                    jac_add(acc, D);
+                }
+            }
+            lp_store_jac(ents, e, lane, acc);
+        }
+    }
+    if (E == 0) return;
+
+    // Affine normalisation of the E entries (simultaneous inversion).
+    fe acc;
+    fe_one(acc);
+    for (int e = 0; e < E; e++) {
+        fe z;
+        lp_load_z(z, ents, e, lane);
+        if (fe_is_zero(z)) fe_one(z);
+        fe_mul(acc, acc, z);
+        lp_store_fe(pref, e, lane, acc);
+    }
+    fe inv;
+    warp_inverse(inv, acc);
+    const size_t tbase = (size_t)s_local * a.emax;
+    for (int e = E - 1; e >= 0; e--) {
+        fe zinv;
+        if (e > 0) {
+            fe pr;
+            lp_load_fe(pr, pref, e - 1, lane);
+            fe_mul(zinv, inv, pr);
+        } else {
+            zinv = inv;
+        }
+        jac Pe;
+        lp_load_jac(Pe, ents, e, lane);
+        fe z = Pe.Z;
+        const bool is_inf = fe_is_zero(z);
+        if (is_inf) fe_one(z);
+        fe_mul(inv, inv, z);
+        aff out;
+        if (is_inf) {
+            fe_zero(out.x);
+            fe_zero(out.y);
+        } else {
+            jac_to_aff_with_zinv(out, Pe, zinv);
+        }
+        store_aff(a.table, a.table_points, ((tbase + e) * 2 + c) * a.lp + j, out);
+    }
+}
+
+struct GatherArgs {
+    int m, l, lp, njb, emax;
+    int s0, nstrips_chunk;
+    bool first;
+    const uint4* table;
+    size_t table_points;
+    uint4* ctC;            // Jacobian ciphertext matrix m x l
+};
+
+__global__ void __launch_bounds__(128) gather_kernel(GatherArgs a, PlanPtrs P) {
+    const unsigned lane = threadIdx.x & 31u;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long total = (long long)a.m * 2 * a.njb;
+    if (gw >= total) return;
+    const int i = (int)(gw / (2 * a.njb));
+    const int rem = (int)(gw % (2 * a.njb));
+    const int c = rem / a.njb, jb = rem % a.njb;
+    const int j = jb * 32 + (int)lane;
+    const size_t ml = (size_t)a.m * a.l;
+    uint4* Cc = a.ctC + (size_t)c * 6 * ml;
+    jac acc;
+    if (a.first || j >= a.l) jac_set_inf(acc);
+    else load_jac(acc, Cc, ml, (size_t)i * a.l + j);
+    const uint16_t* rk = P.rank + (size_t)a.s0 * a.m + i;
+    aff T;
+    for (int sl = 0; sl < a.nstrips_chunk; sl++) {
+        const uint16_t code = rk[(size_t)sl * a.m];
+        if (code == NO_RANK) continue;
+        load_aff(T, a.table, a.table_points, (((size_t)sl * a.emax + code) * 2 + c) * a.lp + j);
+        jac_madd(acc, T);
+    }
+    if (j < a.l) store_jac(Cc, ml, (size_t)i * a.l + j, acc);
+}
+
+// Expected number of distinct non-zero values when m values are drawn
+// uniformly from [0, 2^bits).
+double expected_distinct_nonzero(int m, int bits) {
+    const double V = ldexp(1.0, bits);
+    const double present = V * (1.0 - pow(1.0 - 1.0 / V, (double)m));
+    const double zero = 1.0 - pow(1.0 - 1.0 / V, (double)m);
+    double d = present - zero;
+    return d < 0 ? 0 : d;
+}
+
+// Modelled work in field multiplications (a squaring counted as one).
+double model_cost(int m, int n, int l, int w, int k) {
+    const double MADD = 11, ADD = 16, DBL = 8, NORM = 7;
+    const double chains = 2.0 * l;
+    const int nstrips = (n + k - 1) / k;
+    const double n1 = expected_distinct_nonzero(m, w);
+    const double E = k == 1 ? n1 : expected_distinct_nonzero(m, w * k);
+    double col = n * chains * (n1 * ADD + 2.0 * w * DBL);
+    double tup = k > 1 ? nstrips * chains * E * (k - 1) * ADD : 0.0;
+    double norm = nstrips * chains * E * NORM;
+    double nz = 1.0 - ldexp(1.0, -w * k);
+    double gather = (double)m * chains * nstrips * nz * MADD;
+    return col + tup + norm + gather;
+}
+
+}  // namespace
+
+extern "C" int pcmm_cussen_choose_k(int m, int n, int l, int w) {
+    if (m < 1 || n < 1 || l < 1 || w < 1 || w > PCMM_MAX_W) return 0;
+    int best = 1;
+    double bc = model_cost(m, n, l, w, 1);
+    for (int k = 2; w * k <= PCMM_MAX_WK && k <= n; k++) {
+        double c = model_cost(m, n, l, w, k);
+        if (c < bc) { bc = c; best = k; }
+    }
+    return best;
+}
+
+static const size_t TARGET_ITEMS = 4096;
+
+extern "C" size_t pcmm_cussen_workspace_bytes(int m, int n, int l, int w, int k) {
+    if (k == 0) k = pcmm_cussen_choose_k(m, n, l, w);
+    Layout L;
+    if (!make_layout(L, m, n, l, w, k)) return 0;
+    size_t S = (TARGET_ITEMS + L.items_per_strip - 1) / L.items_per_strip;
+    if (S > (size_t)L.nstrips) S = L.nstrips;
+    if (S < 1) S = 1;
+    return L.plan_bytes + S * L.per_strip_bytes;
+}
+
+extern "C" pcmm_status pcmm_cussen(const uint8_t* A, int m, int n, int w, const uint32_t* ctB, int l,
+                                   uint32_t* ctC, int k, void* ws, size_t ws_bytes,
+                                   pcmm_stream_t stream) {
+    if (!A || !ctB || !ctC || !ws || ((uintptr_t)ws & 255u)) return PCMM_EINVAL;
+    if (m < 1 || n < 1 || l < 1 || w < 1 || w > PCMM_MAX_W) return PCMM_EINVAL;
+    if (k == 0) k = pcmm_cussen_choose_k(m, n, l, w);
+    Layout L;
+    if (!make_layout(L, m, n, l, w, k)) return PCMM_EINVAL;
+    if (ws_bytes < L.plan_bytes + L.per_strip_bytes) return PCMM_ENOMEM;
+    size_t S = (ws_bytes - L.plan_bytes) / L.per_strip_bytes;
+    if (S > (size_t)L.nstrips) S = L.nstrips;
+    cudaStream_t st = (cudaStream_t)stream;
+    PlanPtrs P = plan_ptrs(L, ws);
+    uint8_t* chunk = (uint8_t*)ws + L.plan_bytes;
+    uint4* scratch = (uint4*)chunk;
+    uint4* table = (uint4*)(chunk + align256(S * L.items_per_strip * L.item_u4 * 16));
+    if (cudaMemsetAsync(P.status, 0, 4, st) != cudaSuccess) return PCMM_ECUDA;
+    plan_kernel<<<L.nstrips, PLAN_THREADS, 0, st>>>(A, m, n, w, k, L.emax, P);
+    PCMM_CUDA_CHECK_LAUNCH();
+    for (int s0 = 0; s0 < L.nstrips; s0 += (int)S) {
+        const int sc = (int)((size_t)(L.nstrips - s0) < S ? (size_t)(L.nstrips - s0) : S);
+        TableArgs ta;
+        ta.ctB = (const uint4*)ctB;
+        ta.A = A;
+        ta.m = m; ta.n = n; ta.l = l; ta.w = w; ta.k = k;
+        ta.lp = L.lp; ta.njb = L.njb; ta.n1max = L.n1max; ta.l2max = L.l2max; ta.emax = L.emax;
+        ta.s0 = s0; ta.nstrips_chunk = sc;
+        ta.scratch = scratch;
+        ta.item_u4 = L.item_u4;
+        ta.table = table;
+        ta.table_points = S * L.table_points_per_strip;
+        const long long items = (long long)sc * L.items_per_strip;
+        table_kernel<<<(unsigned)((items + 3) / 4), 128, 0, st>>>(ta, P);
+        PCMM_CUDA_CHECK_LAUNCH();
+        GatherArgs ga;
+        ga.m = m; ga.l = l; ga.lp = L.lp; ga.njb = L.njb; ga.emax = L.emax;
+        ga.s0 = s0; ga.nstrips_chunk = sc;
+        ga.first = (s0 == 0);
+        ga.table = table;
+        ga.table_points = ta.table_points;
+        ga.ctC = (uint4*)ctC;
+        const long long warps = (long long)m * 2 * L.njb;
+        gather_kernel<<<(unsigned)((warps + 3) / 4), 128, 0, st>>>(ga, P);
+        PCMM_CUDA_CHECK_LAUNCH();
+    }
+    return PCMM_OK;
+}
+
+extern "C" pcmm_status pcmm_workspace_status(const void* ws, uint32_t* status_host, pcmm_stream_t stream) {
+    if (!ws || !status_host) return PCMM_EINVAL;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return PCMM_ECUDA;
+    if (cudaMemcpy(status_host, ws, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return PCMM_ECUDA;
+    return PCMM_OK;
+}

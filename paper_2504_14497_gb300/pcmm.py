@@ -1,0 +1,270 @@
+"""Thin Python binding of ``libpcmm.so`` (declared in ``include/pcmm.h``).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels behind the C ABI.  PyTorch provides device memory and the current
+CUDA stream.  Device arrays are ``torch.int32`` tensors holding the uint32
+words of the quad-planar layouts described in ``include/pcmm.h``.
+
+The library must have been built (``paper_2504_14497_gb300.build.build()``);
+there is no fallback: a missing library or a non-zero status raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpcmm.so")
+
+PCMM_AFF_WORDS = 32
+PCMM_JAC_WORDS = 48
+
+# Names of every exported entry point, in the order of include/pcmm.h.
+EXPORTS = (
+    "pcmm_version", "pcmm_status_string", "pcmm_init", "pcmm_keytable_bytes", "pcmm_keytable",
+    "pcmm_encrypt", "pcmm_schoolbook", "pcmm_cussen_choose_k", "pcmm_cussen_workspace_bytes",
+    "pcmm_cussen", "pcmm_workspace_status", "pcmm_normalize", "pcmm_test_field", "pcmm_test_point",
+)
+
+_lock = threading.Lock()
+_lib = None
+
+
+class PcmmError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+def lib():
+    """The loaded library (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"{LIB_PATH} is missing: build it with paper_2504_14497_gb300.build.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            vp, sz, ci, u32p = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_uint32)
+            sig = {
+                "pcmm_version": ([], ci),
+                "pcmm_status_string": ([ci], ctypes.c_char_p),
+                "pcmm_init": ([ci], ci),
+                "pcmm_keytable_bytes": ([], sz),
+                "pcmm_keytable": ([u32p, vp, vp], ci),
+                "pcmm_encrypt": ([vp, vp, vp, sz, vp, vp], ci),
+                "pcmm_schoolbook": ([vp, ci, ci, ci, vp, ci, vp, vp], ci),
+                "pcmm_cussen_choose_k": ([ci, ci, ci, ci], ci),
+                "pcmm_cussen_workspace_bytes": ([ci, ci, ci, ci, ci], sz),
+                "pcmm_cussen": ([vp, ci, ci, ci, vp, ci, vp, ci, vp, sz, vp], ci),
+                "pcmm_workspace_status": ([vp, u32p, vp], ci),
+                "pcmm_normalize": ([vp, sz, vp, vp], ci),
+                "pcmm_test_field": ([ci, vp, vp, vp, sz, vp], ci),
+                "pcmm_test_point": ([ci, vp, vp, vp, vp, sz, vp], ci),
+            }
+            for name, (args, res) in sig.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return lib().pcmm_status_string(int(status)).decode()
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        raise PcmmError(status, what)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def version() -> int:
+    return int(lib().pcmm_version())
+
+
+def init(device: int = 0):
+    _check(lib().pcmm_init(int(device)), "pcmm_init")
+
+
+# ----------------------------------------------------------------- layouts
+
+def points_to_planar(aos: np.ndarray) -> np.ndarray:
+    """uint32[count, 4*Q] point words (coordinates in order) -> [Q, count, 4]."""
+    aos = np.ascontiguousarray(aos, dtype=np.uint32)
+    count, words = aos.shape
+    return np.ascontiguousarray(aos.reshape(count, words // 4, 4).transpose(1, 0, 2))
+
+
+def planar_to_points(pl: np.ndarray) -> np.ndarray:
+    pl = np.asarray(pl, dtype=np.uint32)
+    q, count, _ = pl.shape
+    return np.ascontiguousarray(pl.transpose(1, 0, 2).reshape(count, 4 * q))
+
+
+def ct_to_planar(ct: np.ndarray) -> np.ndarray:
+    """uint32[..., 2, 16] affine (or [..., 2, 24] Jacobian) ciphertexts ->
+    the flat uint32 array of the quad-planar ciphertext layout."""
+    ct = np.asarray(ct, dtype=np.uint32)
+    words = ct.shape[-1]
+    flat = ct.reshape(-1, 2, words)
+    count = flat.shape[0]
+    pl = flat.reshape(count, 2, words // 4, 4).transpose(1, 2, 0, 3)
+    return np.ascontiguousarray(pl).reshape(-1)
+
+
+def planar_to_ct(flat: np.ndarray, count: int, jacobian: bool = False) -> np.ndarray:
+    """Inverse of ct_to_planar: returns uint32[count, 2, 16 or 24]."""
+    q = 6 if jacobian else 4
+    pl = np.asarray(flat, dtype=np.uint32).reshape(2, q, count, 4)
+    return np.ascontiguousarray(pl.transpose(2, 0, 1, 3).reshape(count, 2, 4 * q))
+
+
+def scalars_to_planar(r: np.ndarray) -> np.ndarray:
+    """uint32[..., 8] scalars -> flat quad-planar uint32[8 * count]."""
+    r = np.asarray(r, dtype=np.uint32).reshape(-1, 8)
+    count = r.shape[0]
+    return np.ascontiguousarray(r.reshape(count, 2, 4).transpose(1, 0, 2)).reshape(-1)
+
+
+def to_device_words(a: np.ndarray, device="cuda"):
+    """Host uint32 words -> device int32 tensor (same bits)."""
+    torch = _torch()
+    a = np.ascontiguousarray(a, dtype=np.uint32)
+    return torch.from_numpy(a.view(np.int32)).to(device)
+
+
+def to_host_words(t) -> np.ndarray:
+    return t.detach().cpu().numpy().view(np.uint32)
+
+
+# ------------------------------------------------------------- encryption
+
+def keytable_bytes() -> int:
+    return int(lib().pcmm_keytable_bytes())
+
+
+def keytable(H: np.ndarray, device="cuda", stream=None):
+    """Comb table of the public key H (uint32[16], x then y)."""
+    torch = _torch()
+    H = np.ascontiguousarray(H, dtype=np.uint32)
+    tab = torch.empty(keytable_bytes(), dtype=torch.uint8, device=device)
+    _check(lib().pcmm_keytable(H.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), _ptr(tab),
+                               _stream(stream)), "pcmm_keytable")
+    return tab
+
+
+def encrypt(table, msg, r_planar, out=None, stream=None):
+    """msg: cuda uint8[count]; r_planar: cuda int32[8 * count] (quad-planar
+    scalars).  Returns the affine ciphertext array, cuda int32[32 * count]."""
+    torch = _torch()
+    count = msg.numel()
+    if r_planar.numel() != 8 * count:
+        raise ValueError("r must hold 8 words per message")
+    if out is None:
+        out = torch.empty(PCMM_AFF_WORDS * count, dtype=torch.int32, device=msg.device)
+    _check(lib().pcmm_encrypt(_ptr(table), _ptr(msg), _ptr(r_planar), count, _ptr(out),
+                              _stream(stream)), "pcmm_encrypt")
+    return out
+
+
+# ------------------------------------------------------------------ PC-MM
+
+def schoolbook(A, ctB, l: int, w: int, out=None, stream=None):
+    """A: cuda uint8[m, n]; ctB: cuda int32[32 * n * l].  Returns the
+    Jacobian ciphertext matrix, cuda int32[48 * m * l]."""
+    torch = _torch()
+    m, n = A.shape
+    if out is None:
+        out = torch.empty(PCMM_JAC_WORDS * m * l, dtype=torch.int32, device=A.device)
+    _check(lib().pcmm_schoolbook(_ptr(A), m, n, w, _ptr(ctB), l, _ptr(out), _stream(stream)),
+           "pcmm_schoolbook")
+    return out
+
+
+def choose_k(m: int, n: int, l: int, w: int) -> int:
+    return int(lib().pcmm_cussen_choose_k(m, n, l, w))
+
+
+def workspace_bytes(m: int, n: int, l: int, w: int, k: int = 0) -> int:
+    return int(lib().pcmm_cussen_workspace_bytes(m, n, l, w, k))
+
+
+def workspace(m: int, n: int, l: int, w: int, k: int = 0, device="cuda"):
+    torch = _torch()
+    nb = workspace_bytes(m, n, l, w, k)
+    if nb == 0:
+        raise ValueError("invalid PC-MM shape")
+    return torch.empty(nb, dtype=torch.uint8, device=device)
+
+
+def cussen(A, ctB, l: int, w: int, k: int = 0, ws=None, out=None, stream=None):
+    """Cussen PC-MM.  Same arguments and result as ``schoolbook`` plus the
+    strip width k (0: cost model) and an optional workspace tensor."""
+    torch = _torch()
+    m, n = A.shape
+    if ws is None:
+        ws = workspace(m, n, l, w, k, device=A.device)
+    if out is None:
+        out = torch.empty(PCMM_JAC_WORDS * m * l, dtype=torch.int32, device=A.device)
+    _check(lib().pcmm_cussen(_ptr(A), m, n, w, _ptr(ctB), l, _ptr(out), k, _ptr(ws), ws.numel(),
+                             _stream(stream)), "pcmm_cussen")
+    return out
+
+
+def workspace_status(ws, stream=None) -> int:
+    v = ctypes.c_uint32(0)
+    _check(lib().pcmm_workspace_status(_ptr(ws), ctypes.byref(v), _stream(stream)),
+           "pcmm_workspace_status")
+    return int(v.value)
+
+
+def normalize(ct_jac, count: int, out=None, stream=None):
+    torch = _torch()
+    if out is None:
+        out = torch.empty(PCMM_AFF_WORDS * count, dtype=torch.int32, device=ct_jac.device)
+    _check(lib().pcmm_normalize(_ptr(ct_jac), count, _ptr(out), _stream(stream)), "pcmm_normalize")
+    return out
+
+
+# ------------------------------------------------------------- unit tests
+
+def test_field(op: int, a, b=None, stream=None):
+    torch = _torch()
+    count = a.numel() // 8
+    out = torch.empty_like(a)
+    bp = _ptr(b) if b is not None else ctypes.c_void_p(0)
+    _check(lib().pcmm_test_field(op, _ptr(a), bp, _ptr(out), count, _stream(stream)), "pcmm_test_field")
+    return out
+
+
+def test_point(op: int, P, Q=None, k=None, count: int = 0, stream=None):
+    torch = _torch()
+    out = torch.empty(16 * count, dtype=torch.int32, device=P.device)
+    qp = _ptr(Q) if Q is not None else ctypes.c_void_p(0)
+    kp = _ptr(k) if k is not None else ctypes.c_void_p(0)
+    _check(lib().pcmm_test_point(op, _ptr(P), qp, kp, _ptr(out), count, _stream(stream)),
+           "pcmm_test_point")
+    return out

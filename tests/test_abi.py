@@ -1,0 +1,77 @@
+"""CPU checks of the boundary: the C-ABI library loads and exports every
+function declared in include/pcmm.h (no compute call, no GPU), the host-side
+argument validation rejects bad shapes without launching anything, and the
+Python layout helpers round-trip."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2504_14497_gb300 import build as pkg_build
+from paper_2504_14497_gb300 import pcmm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pkg_build.build()
+    return pcmm.lib()
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "pcmm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pcmm_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert "pcmm_cussen" in names and "pcmm_normalize" in names
+    for nm in names:
+        assert hasattr(lib, nm), nm
+    assert set(pcmm.EXPORTS) <= set(names)
+
+
+def test_version_and_status_strings(lib):
+    assert pcmm.version() >= 10000
+    assert pcmm.status_string(0) == "PCMM_OK"
+    assert "workspace" in pcmm.status_string(2)
+    assert pcmm.status_string(99) == "unknown pcmm status"
+
+
+def test_host_validation_without_gpu(lib):
+    # Invalid shapes are rejected before any CUDA call.
+    assert pcmm.workspace_bytes(0, 4, 4, 4, 1) == 0
+    assert pcmm.workspace_bytes(4, 4, 4, 9, 1) == 0
+    assert pcmm.workspace_bytes(4, 4, 4, 4, 4) == 0   # w * k = 16 > 12
+    assert pcmm.workspace_bytes(4, 4, 4, 4, 3) > 0
+    assert lib.pcmm_cussen(None, 4, 4, 4, None, 4, None, 1, None, 0, None) == 1
+    assert lib.pcmm_schoolbook(None, 4, 4, 4, None, 4, None, None) == 1
+    assert lib.pcmm_normalize(None, 4, None, None) == 1
+
+
+def test_cost_model_choices(lib):
+    # Wide values: one column per strip; narrow values: wider strips.
+    assert pcmm.choose_k(1024, 1024, 256, 8) == 1
+    assert pcmm.choose_k(1024, 1024, 256, 4) >= 2
+    assert pcmm.choose_k(1024, 1024, 256, 1) >= 4
+    for w in range(1, 9):
+        k = pcmm.choose_k(100, 50, 20, w)
+        assert 1 <= k and w * k <= 12
+
+
+def test_layout_helpers_round_trip():
+    rng = np.random.default_rng(0)
+    ct = rng.integers(0, 2**32, size=(7, 2, 16), dtype=np.uint64).astype(np.uint32)
+    flat = pcmm.ct_to_planar(ct)
+    assert flat.shape == (7 * 32,)
+    # quad q of C2 of element i sits at word offset 16*count + 4*(q*count + i)
+    assert (flat[16 * 7 + 4 * (2 * 7 + 3): 16 * 7 + 4 * (2 * 7 + 3) + 4] == ct[3, 1, 8:12]).all()
+    assert (pcmm.planar_to_ct(flat, 7) == ct).all()
+    jc = rng.integers(0, 2**32, size=(5, 2, 24), dtype=np.uint64).astype(np.uint32)
+    assert (pcmm.planar_to_ct(pcmm.ct_to_planar(jc), 5, jacobian=True) == jc).all()
+    r = rng.integers(0, 2**32, size=(6, 8), dtype=np.uint64).astype(np.uint32)
+    rp = pcmm.scalars_to_planar(r)
+    assert (rp[4 * 6 + 4 * 2: 4 * 6 + 4 * 2 + 4] == r[2, 4:8]).all()
