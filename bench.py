@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Throughput benchmark of encrypted PC-MM (Cussen's method) on GB300.
+
+Workload (one step): the single large PC-MM, A 1024 x 1024 with unsigned
+w-bit entries for each w in {1, 2, 4, 8}, times Enc(B) 1024 x 256 (8-bit
+messages, EC-ElGamal over P-256), Cussen with the cost model's strip width,
+followed by affine normalisation of the 1024 x 256 output ciphertexts.
+Inputs are seeded and synthetic.  The metric is point additions (of two
+finite points, including the doublings of the compressed-value
+multiplications) performed per second; the dominant kernel's rate is also
+reported against the integer multiply-add (IMAD) roofline.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs the same workload on its own GPU
+(replicas, no collective on the data path) and rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "encrypted PC-MM ciphertext point-adds/s and % int/HBM roofline (bit-exact) vs plain"
+UNIT = "point-adds/s"
+IMAD_PER_SM_PER_CLK = 64      # 32-bit integer multiply-add lanes per SM per clock
+SEED = 2504144970 + 2         # the large single PC-MM workload
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--widths", default="1,2,4,8")
+    ap.add_argument("--shape", default="1024,1024,256", help="m,n,l")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-schoolbook", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------ distributed
+
+class Dist:
+    def __init__(self, gpus):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            dist.init_process_group("gloo", rank=self.rank, world_size=self.world)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.sw_power_cap,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["sw_power_cap", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# -------------------------------------------------------------- workload
+
+def make_problem(m, n, l, widths):
+    from paper_2504_14497_gb300 import inputs
+    pr = {w: inputs.pcmm_problem(SEED, m, n, l, w) for w in widths}
+    return pr
+
+
+_CPU_CT = {}
+
+
+def cpu_sample(problem, w, m_s, l_s, k):
+    """The CPU oracle on a bounded sample of the workload: the first m_s rows
+    of A and the first l_s columns of Enc(B) (encrypted by the oracle, once,
+    outside the timing).  Returns (point additions, seconds)."""
+    from oracle import oracle
+    A = problem["A"][:m_s]
+    key = (id(problem), l_s)
+    if key not in _CPU_CT:
+        H = oracle.keygen(problem["sk"])
+        _CPU_CT[key] = oracle.encrypt(H, problem["B"][:, :l_s], problem["r"][:, :l_s])
+    ct = _CPU_CT[key]
+    t0 = time.perf_counter()
+    _, cnt = oracle.cussen(A, ct, w, k)
+    dt = time.perf_counter() - t0
+    adds = cnt["ecsm_dbl"] + cnt["ecsm_add"] + cnt["recon_add"] + cnt["accum_add"]
+    return adds, dt
+
+
+def run_reference(args, dist):
+    """The CPU oracle as it stands, timed on the host cores."""
+    m, n, l = (int(x) for x in args.shape.split(","))
+    if dist.rank != 0:
+        return None
+    from oracle import oracle
+    from paper_2504_14497_gb300 import inputs
+    w, m_s, l_s, k = 4, 64, 16, 2
+    problem = inputs.pcmm_problem(SEED, m, n, l, w)
+    for _ in range(args.warmup):
+        cpu_sample(problem, w, m_s, l_s, k)
+    adds_tot, sec_tot = 0, 0.0
+    for _ in range(args.steps):
+        a, s = cpu_sample(problem, w, m_s, l_s, k)
+        adds_tot += a
+        sec_tot += s
+    value = adds_tot / sec_tot
+    sample = f"w=4 k=2 Cussen, rows 0..{m_s - 1} x Enc(B) columns 0..{l_s - 1} of the {m}x{n}x{l} workload"
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec_tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (seeded)",
+        "config": {"workload": f"single large PC-MM {m}x{n}x{l}, CPU oracle sample", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def run_ours(args, dist):
+    import torch
+
+    from paper_2504_14497_gb300 import build, counts, pcmm
+
+    build.build()
+    dev_index = dist.local if torch.cuda.device_count() > dist.local else 0
+    torch.cuda.set_device(dev_index)
+    dev = torch.device("cuda", dev_index)
+    pcmm.init(dev_index)
+    m, n, l = (int(x) for x in args.shape.split(","))
+    widths = [int(x) for x in args.widths.split(",")]
+    problems = make_problem(m, n, l, widths)
+    base = problems[widths[0]]
+    H = pcmm.public_key(base["sk"], device=dev)
+    tab = pcmm.keytable(H, device=dev)
+    msg = torch.from_numpy(base["B"].reshape(-1)).to(dev)
+    rr = pcmm.to_device_words(pcmm.scalars_to_planar(base["r"]), dev)
+    ctB = pcmm.encrypt(tab, msg, rr)
+    stream = torch.cuda.current_stream()
+    runs = []
+    for w in widths:
+        k = pcmm.choose_k(m, n, l, w)
+        A = torch.from_numpy(problems[w]["A"]).to(dev)
+        ws = pcmm.workspace(m, n, l, w, k, device=dev)
+        jac = torch.empty(48 * m * l, dtype=torch.int32, device=dev)
+        aff = torch.empty(32 * m * l, dtype=torch.int32, device=dev)
+        c = counts.cussen_counts(problems[w]["A"], w, k, l)
+        runs.append(dict(w=w, k=k, A=A, ws=ws, jac=jac, aff=aff, counts=c))
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def step():
+        for r in runs:
+            pcmm.cussen(r["A"], ctB, l, r["w"], k=r["k"], ws=r["ws"], out=r["jac"])
+            pcmm.normalize(r["jac"], m * l, out=r["aff"])
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    for r in runs:
+        if pcmm.workspace_status(r["ws"]) != 0:
+            raise RuntimeError("device status word set during warm-up")
+
+    # ---- timed region: K steps, L2 flushed between steps (outside events)
+    clocks = ClockSampler(dev_index)
+    pcmm.profile_enable(64 * args.steps * len(widths) + 64)
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    total_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    dist.barrier()
+    prof = pcmm.profile_read()
+    pcmm.profile_enable(0)
+    total_ms = dist.max(total_ms)
+
+    ops_step = sum(counts.point_ops(r["counts"]) for r in runs)
+    value = dist.world * ops_step * args.steps / (total_ms / 1e3)
+    launches = sum(v[1] for v in prof.values())
+
+    # ---- roofline of the dominant kernel (integer multiply-add bound)
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak = props.multi_processor_count * IMAD_PER_SM_PER_CLK * sm_max * 1e6
+    kern = {"gather": sum(counts.gather_imad(r["counts"]) for r in runs),
+            "table": sum(counts.table_imad(r["counts"]) for r in runs)}
+    dom = max(kern, key=lambda nm: prof[nm][0])
+    dom_ms, dom_launches = prof[dom]
+    achieved = kern[dom] * args.steps / (dom_ms / 1e3)
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved / 1e12,
+                "peak": peak / 1e12, "unit": "TIMAD/s", "frac": achieved / peak,
+                "traffic": None, "launches": dom_launches,
+                "avg_launch_ms": dom_ms / max(dom_launches, 1),
+                "peak_basis": f"{props.multi_processor_count} SMs x {IMAD_PER_SM_PER_CLK} IMAD/clk x {sm_max:.0f} MHz"}
+    kernels = {nm: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+               for nm, v in prof.items() if v[1]}
+    for nm in ("gather", "table"):
+        if nm in kernels:
+            kernels[nm]["frac_imad_peak"] = kern[nm] * args.steps / (prof[nm][0] / 1e3) / peak
+
+    # ---- schoolbook on the same GPU (context: Cussen speed-up, w = 8 and 4)
+    schoolbook = None
+    if not args.no_schoolbook and dist.rank == 0:
+        schoolbook = {}
+        for r in runs:
+            if r["w"] not in (4, 8):
+                continue
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            pcmm.schoolbook(r["A"], ctB, l, r["w"], out=r["jac"])
+            ev1.record(stream)
+            ev1.synchronize()
+            ev2, ev3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev2.record(stream)
+            pcmm.cussen(r["A"], ctB, l, r["w"], k=r["k"], ws=r["ws"], out=r["jac"])
+            ev3.record(stream)
+            ev3.synchronize()
+            sb, cu = ev0.elapsed_time(ev1), ev2.elapsed_time(ev3)
+            schoolbook[f"w{r['w']}"] = {"schoolbook_ms": sb, "cussen_ms": cu, "speedup": sb / cu}
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        hA = [torch.from_numpy(problems[r["w"]]["A"]).pin_memory() for r in runs]
+        hB = pcmm.to_host_words(ctB).view(np.int32)
+        hB = torch.from_numpy(hB.copy()).pin_memory()
+        hC = [torch.empty(32 * m * l, dtype=torch.int32).pin_memory() for _ in runs]
+        dB = torch.empty_like(ctB)
+        dA = [torch.empty_like(r["A"]) for r in runs]
+
+        def e2e_step():
+            dB.copy_(hB, non_blocking=True)
+            for r, a_h, a_d, c_h in zip(runs, hA, dA, hC):
+                a_d.copy_(a_h, non_blocking=True)
+                pcmm.cussen(a_d, dB, l, r["w"], k=r["k"], ws=r["ws"], out=r["jac"])
+                pcmm.normalize(r["jac"], m * l, out=r["aff"])
+                c_h.copy_(r["aff"], non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        dist.barrier()
+        e2e_ms = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            e2e_step()
+            ev1.record(stream)
+            ev1.synchronize()
+            e2e_ms += ev0.elapsed_time(ev1)
+        e2e_ms = dist.max(e2e_ms)
+        e2e = {"value": dist.world * ops_step * args.steps / (e2e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(hB.numel() * 4 + sum(a.numel() for a in hA)),
+               "d2h_bytes_per_step": int(sum(c.numel() * 4 for c in hC)),
+               "ms_per_step": e2e_ms / args.steps}
+
+    # ---- CPU oracle baseline on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if not args.no_cpu_baseline and dist.world == 1:
+        from oracle import oracle
+        w_s = 4 if 4 in problems else widths[0]
+        m_s, l_s, k_s = 128, 16, pcmm.choose_k(m, n, l, w_s)
+        adds, sec = cpu_sample(problems[w_s], w_s, m_s, l_s, k_s)
+        cpu = {"value": adds / sec, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+               "sample": f"w={w_s} k={k_s} Cussen on rows 0..{m_s - 1} x Enc(B) columns 0..{l_s - 1}"
+                         f" of the {m}x{n}x{l} workload ({adds} point additions, {sec:.1f} s)"}
+
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded)",
+        "config": {"workload": f"single large PC-MM A {m}x{n} (w in {widths}) x Enc(B) {n}x{l}, "
+                               f"EC-ElGamal P-256, Cussen + affine normalisation",
+                   "m": m, "n": n, "l": l, "widths": widths,
+                   "k": {f"w{r['w']}": r["k"] for r in runs},
+                   "l2": "flushed between timed steps (512 MiB write outside the events)",
+                   "parallelism": f"replicas x{dist.world}"},
+        "point_ops_per_step": ops_step,
+        "roofline": roofline, "kernels": kernels, "gpu_launches": launches,
+        "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "schoolbook": schoolbook,
+    }
+
+
+def main():
+    args = parse()
+    dist = Dist(args.gpus)
+    try:
+        out = run_reference(args, dist) if args.impl == "reference" else run_ours(args, dist)
+        if dist.rank == 0 and out is not None:
+            print(json.dumps(out), flush=True)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -105,6 +105,14 @@ pcmm_status pcmm_keytable(const uint32_t *H_host, void *keytable, pcmm_stream_t 
 pcmm_status pcmm_encrypt(const void *keytable, const uint8_t *msg, const uint32_t *r, size_t count,
                          uint32_t *ct, pcmm_stream_t stream);
 
+/* Multiplies the generator by count scalars: points[i] = s_i G (KeyGen,
+ * Section 2.4: the public key is H = x G for the secret key x).
+ * scalars: device, quad-planar (8 * count words), each used modulo q.
+ * points: device, affine point array of count points (16 * count words).
+ * Requires pcmm_init on the current device.  Errors: PCMM_EINVAL, PCMM_ECUDA. */
+pcmm_status pcmm_base_mul(const uint32_t *scalars, size_t count, uint32_t *points,
+                          pcmm_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * PC-MM.  Inputs: A (device uint8 m x n, entries < 2^w), ctB (device affine
  * ciphertext matrix n x l).  Output: ctC (device Jacobian ciphertext matrix
@@ -158,6 +166,21 @@ pcmm_status pcmm_workspace_status(const void *ws, uint32_t *status_host, pcmm_st
  * (may not overlap).  Errors: PCMM_EINVAL, PCMM_ECUDA. */
 pcmm_status pcmm_normalize(const uint32_t *ct_jac, size_t count, uint32_t *ct_aff,
                            pcmm_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Per-kernel timing.  pcmm_profile_enable(capacity > 0) creates `capacity`
+ * pairs of CUDA events; from then on every library kernel launch records a
+ * start and a stop event on its own stream (until the pool is used up).
+ * pcmm_profile_read synchronises those events and writes, for each kernel
+ * id 0..pcmm_kernel_count()-1, the summed milliseconds and the number of
+ * launches (host arrays of pcmm_kernel_count() entries), then recycles the
+ * pool.  pcmm_profile_enable(0) frees the events and disables timing.  Not
+ * thread-safe.  Errors: PCMM_EINVAL, PCMM_ECUDA.
+ * ---------------------------------------------------------------------- */
+pcmm_status pcmm_profile_enable(int capacity);
+pcmm_status pcmm_profile_read(double *ms_host, long long *launches_host);
+int pcmm_kernel_count(void);
+const char *pcmm_kernel_name(int id);
 
 /* ------------------------------------------------------------------------
  * Unit-test entry points for the device arithmetic (device arrays of

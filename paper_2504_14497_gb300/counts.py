@@ -1,0 +1,94 @@
+"""Host-side accounting of the point operations a PC-MM launch performs.
+
+Used to turn measured times into rates (point additions per second) and
+roofline fractions.  It recomputes, from the plaintext matrix A alone, the
+compression plan the plan kernel builds (same definitions), and counts the
+group operations of two finite points that the table and gather kernels
+execute for the l useful output columns.  It does no curve arithmetic and is
+not on the compute path.
+
+Per-operation integer work, in 32x32->64-bit limb products (a field
+multiplication is 64 products, a squaring 36; P-256 special-form reduction
+needs none), each product costing two IMAD instructions (low and high word):
+    mixed addition    (madd-2007-bl, 7M + 4S)   592 products
+    full addition     (add-2007-bl, 11M + 5S)   884 products
+    doubling, a = -3  (dbl-2001-b, 3M + 5S)     372 products
+    normalisation of one table entry (3M for simultaneous inversion,
+      then 1S + 3M for x = X Z^-2, y = Y Z^-3)  420 products
+"""
+from __future__ import annotations
+
+import numpy as np
+
+N_ITER = 4
+PRODUCTS = {"madd": 592, "add": 884, "dbl": 372, "norm": 420}
+IMAD_PER_PRODUCT = 2
+
+
+def _levels(col: np.ndarray, N: int = N_ITER):
+    """Lengths of levels 1..N and the level-N values of one column."""
+    v = np.unique(col[col != 0]).astype(np.int64)
+    lens = [len(v)]
+    for _ in range(1, N):
+        d = np.diff(v, prepend=0) if len(v) else v
+        v = np.unique(d)
+        lens.append(len(v))
+    return lens, v
+
+
+def cussen_counts(A: np.ndarray, w: int, k: int, l: int, N: int = N_ITER) -> dict:
+    A = np.asarray(A).astype(np.int64) & ((1 << w) - 1)
+    m, n = A.shape
+    chains = 2 * l
+    gather = 0
+    tadd = tmadd = tdbl = norm = 0
+    nnz_rows = np.zeros(m, dtype=np.int64)
+    for s0 in range(0, n, k):
+        cols = A[:, s0:s0 + k]
+        codes = np.zeros(m, dtype=np.int64)
+        for t in range(cols.shape[1]):
+            codes |= cols[:, t] << (w * t)
+            lens, vN = _levels(cols[:, t], N)
+            for v in vN:
+                v = int(v)
+                tdbl += chains * (v.bit_length() - 1)
+                tmadd += chains * (bin(v).count("1") - 1)
+            tadd += chains * sum(max(x - 1, 0) for x in lens[:-1])
+        distinct = np.unique(codes[codes != 0])
+        if cols.shape[1] > 1:
+            for code in distinct:
+                parts = sum(1 for t in range(cols.shape[1]) if (int(code) >> (w * t)) & ((1 << w) - 1))
+                tadd += chains * max(parts - 1, 0)
+        norm += chains * len(distinct)
+        nnz_rows += codes != 0
+    gather = chains * int(np.maximum(nnz_rows - 1, 0).sum())
+    return {"gather_madd": gather, "table_add": tadd, "table_madd": tmadd, "table_dbl": tdbl,
+            "table_norm": norm}
+
+
+def point_ops(c: dict) -> int:
+    """Point additions and doublings of two finite points performed."""
+    return c["gather_madd"] + c["table_add"] + c["table_madd"] + c["table_dbl"]
+
+
+def gather_imad(c: dict) -> int:
+    return c["gather_madd"] * PRODUCTS["madd"] * IMAD_PER_PRODUCT
+
+
+def table_imad(c: dict) -> int:
+    p = (c["table_add"] * PRODUCTS["add"] + c["table_madd"] * PRODUCTS["madd"]
+         + c["table_dbl"] * PRODUCTS["dbl"] + c["table_norm"] * PRODUCTS["norm"])
+    return p * IMAD_PER_PRODUCT
+
+
+def schoolbook_counts(A: np.ndarray, l: int) -> dict:
+    """Double-and-add per non-zero entry, then one full addition per term
+    after the first in each output."""
+    A = np.asarray(A).astype(np.int64)
+    nz = A[A != 0]
+    bl = np.floor(np.log2(nz)).astype(np.int64) if nz.size else np.zeros(0, np.int64)
+    pc = np.array([bin(int(v)).count("1") for v in nz], dtype=np.int64) if nz.size else np.zeros(0, np.int64)
+    chains = 2 * l
+    rows_nnz = (A != 0).sum(axis=1)
+    return {"dbl": chains * int(bl.sum()), "madd": chains * int((pc - 1).sum()),
+            "add": chains * int(np.maximum(rows_nnz - 1, 0).sum())}

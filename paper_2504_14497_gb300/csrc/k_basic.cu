@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "profiler.cuh"
 
 using namespace pcmm;
 
@@ -85,6 +86,30 @@ __global__ void __launch_bounds__(128) encrypt_kernel(const uint4* __restrict__ 
         store_aff(ct, count, i, out[0]);
         store_aff(ct + 4 * count, count, i, out[1]);
     }
+}
+
+// s G for count scalars (key generation: H = x G), one thread per scalar.
+__global__ void __launch_bounds__(128) base_mul_kernel(const uint4* __restrict__ gtab,
+                                                       const uint4* __restrict__ sc, size_t count,
+                                                       uint4* __restrict__ out) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < count;
+    const size_t ii = valid ? i : 0;
+    fe s;
+    fe_from_quads(s, sc[ii], sc[count + ii]);
+    jac P[1];
+    jac_set_inf(P[0]);
+    aff T;
+    for (int win = 0; win < COMB_WINDOWS; win++) {
+        const uint32_t v = (s.v[win >> 2] >> (8 * (win & 3))) & 0xffu;
+        if (v) {
+            load_aff(T, gtab, COMB_POINTS, (size_t)win * COMB_ENTRIES + v);
+            jac_madd(P[0], T);
+        }
+    }
+    aff o[1];
+    warp_normalize_regs<1>(o, P);
+    if (valid) store_aff(out, count, i, o[0]);
 }
 
 // Jacobian ciphertexts -> canonical affine, one thread per ciphertext.
@@ -187,7 +212,10 @@ extern "C" pcmm_status pcmm_init(int device) {
     }
     uint4* tab = nullptr;
     if (cudaGetSymbolAddress((void**)&tab, g_comb_G) != cudaSuccess) return PCMM_ECUDA;
-    comb_build_kernel<<<COMB_POINTS / 128, 128>>>(G, tab);
+    {
+        ProfScope ps(KID_COMB, 0);
+        comb_build_kernel<<<COMB_POINTS / 128, 128>>>(G, tab);
+    }
     PCMM_CUDA_CHECK_LAUNCH();
     if (cudaDeviceSynchronize() != cudaSuccess) return PCMM_ECUDA;
     g_ready[device] = true;
@@ -216,7 +244,10 @@ extern "C" pcmm_status pcmm_keytable(const uint32_t* H_host, void* keytable, pcm
         z |= H_host[i] | H_host[8 + i];
     }
     if (!z) return PCMM_EINVAL;
-    comb_build_kernel<<<COMB_POINTS / 128, 128, 0, (cudaStream_t)stream>>>(H, (uint4*)keytable);
+    {
+        ProfScope ps(KID_COMB, (cudaStream_t)stream);
+        comb_build_kernel<<<COMB_POINTS / 128, 128, 0, (cudaStream_t)stream>>>(H, (uint4*)keytable);
+    }
     PCMM_CUDA_CHECK_LAUNCH();
     return PCMM_OK;
 }
@@ -230,8 +261,25 @@ extern "C" pcmm_status pcmm_encrypt(const void* keytable, const uint8_t* msg, co
     if (dev < 0 || dev >= 64 || !g_ready[dev]) return PCMM_EINVAL;
     uint4* gtab = nullptr;
     if (cudaGetSymbolAddress((void**)&gtab, g_comb_G) != cudaSuccess) return PCMM_ECUDA;
+    ProfScope ps(KID_ENCRYPT, (cudaStream_t)stream);
     encrypt_kernel<<<grid_for(count, 128), 128, 0, (cudaStream_t)stream>>>(
         gtab, (const uint4*)keytable, msg, (const uint4*)r, count, (uint4*)ct);
+    PCMM_CUDA_CHECK_LAUNCH();
+    return PCMM_OK;
+}
+
+extern "C" pcmm_status pcmm_base_mul(const uint32_t* scalars, size_t count, uint32_t* points,
+                                     pcmm_stream_t stream) {
+    if (!scalars || !points) return PCMM_EINVAL;
+    if (count == 0) return PCMM_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PCMM_ECUDA;
+    if (dev < 0 || dev >= 64 || !g_ready[dev]) return PCMM_EINVAL;
+    uint4* gtab = nullptr;
+    if (cudaGetSymbolAddress((void**)&gtab, g_comb_G) != cudaSuccess) return PCMM_ECUDA;
+    ProfScope ps(KID_ENCRYPT, (cudaStream_t)stream);
+    base_mul_kernel<<<grid_for(count, 128), 128, 0, (cudaStream_t)stream>>>(
+        gtab, (const uint4*)scalars, count, (uint4*)points);
     PCMM_CUDA_CHECK_LAUNCH();
     return PCMM_OK;
 }
@@ -240,6 +288,7 @@ extern "C" pcmm_status pcmm_normalize(const uint32_t* ct_jac, size_t count, uint
                                       pcmm_stream_t stream) {
     if (!ct_jac || !ct_aff) return PCMM_EINVAL;
     if (count == 0) return PCMM_OK;
+    ProfScope ps(KID_NORMALIZE, (cudaStream_t)stream);
     normalize_kernel<<<grid_for(count, 128), 128, 0, (cudaStream_t)stream>>>(
         (const uint4*)ct_jac, count, (uint4*)ct_aff);
     PCMM_CUDA_CHECK_LAUNCH();

@@ -34,6 +34,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "profiler.cuh"
 
 using namespace pcmm;
 
@@ -487,7 +488,10 @@ extern "C" pcmm_status pcmm_cussen(const uint8_t* A, int m, int n, int w, const 
     uint4* scratch = (uint4*)chunk;
     uint4* table = (uint4*)(chunk + align256(S * L.items_per_strip * L.item_u4 * 16));
     if (cudaMemsetAsync(P.status, 0, 4, st) != cudaSuccess) return PCMM_ECUDA;
-    plan_kernel<<<L.nstrips, PLAN_THREADS, 0, st>>>(A, m, n, w, k, L.emax, P);
+    {
+        ProfScope ps(KID_PLAN, st);
+        plan_kernel<<<L.nstrips, PLAN_THREADS, 0, st>>>(A, m, n, w, k, L.emax, P);
+    }
     PCMM_CUDA_CHECK_LAUNCH();
     for (int s0 = 0; s0 < L.nstrips; s0 += (int)S) {
         const int sc = (int)((size_t)(L.nstrips - s0) < S ? (size_t)(L.nstrips - s0) : S);
@@ -502,7 +506,10 @@ extern "C" pcmm_status pcmm_cussen(const uint8_t* A, int m, int n, int w, const 
         ta.table = table;
         ta.table_points = S * L.table_points_per_strip;
         const long long items = (long long)sc * L.items_per_strip;
-        table_kernel<<<(unsigned)((items + 3) / 4), 128, 0, st>>>(ta, P);
+        {
+            ProfScope ps(KID_TABLE, st);
+            table_kernel<<<(unsigned)((items + 3) / 4), 128, 0, st>>>(ta, P);
+        }
         PCMM_CUDA_CHECK_LAUNCH();
         GatherArgs ga;
         ga.m = m; ga.l = l; ga.lp = L.lp; ga.njb = L.njb; ga.emax = L.emax;
@@ -512,7 +519,10 @@ extern "C" pcmm_status pcmm_cussen(const uint8_t* A, int m, int n, int w, const 
         ga.table_points = ta.table_points;
         ga.ctC = (uint4*)ctC;
         const long long warps = (long long)m * 2 * L.njb;
-        gather_kernel<<<(unsigned)((warps + 3) / 4), 128, 0, st>>>(ga, P);
+        {
+            ProfScope ps(KID_GATHER, st);
+            gather_kernel<<<(unsigned)((warps + 3) / 4), 128, 0, st>>>(ga, P);
+        }
         PCMM_CUDA_CHECK_LAUNCH();
     }
     return PCMM_OK;

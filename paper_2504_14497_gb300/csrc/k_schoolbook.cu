@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "profiler.cuh"
 
 using namespace pcmm;
 
@@ -51,6 +52,7 @@ extern "C" pcmm_status pcmm_schoolbook(const uint8_t* A, int m, int n, int w, co
     const long long warps = (long long)m * 2 * ((l + 31) / 32);
     const long long blocks = (warps + 3) / 4;
     if (blocks > 0x7fffffffLL) return PCMM_EUNSUPPORTED;
+    ProfScope ps(KID_SCHOOLBOOK, (cudaStream_t)stream);
     schoolbook_kernel<<<(unsigned)blocks, 128, 0, (cudaStream_t)stream>>>(
         A, m, n, (const uint4*)ctB, l, (uint4*)ctC, (1u << w) - 1u);
     PCMM_CUDA_CHECK_LAUNCH();

@@ -25,8 +25,9 @@ PCMM_JAC_WORDS = 48
 # Names of every exported entry point, in the order of include/pcmm.h.
 EXPORTS = (
     "pcmm_version", "pcmm_status_string", "pcmm_init", "pcmm_keytable_bytes", "pcmm_keytable",
-    "pcmm_encrypt", "pcmm_schoolbook", "pcmm_cussen_choose_k", "pcmm_cussen_workspace_bytes",
-    "pcmm_cussen", "pcmm_workspace_status", "pcmm_normalize", "pcmm_test_field", "pcmm_test_point",
+    "pcmm_encrypt", "pcmm_base_mul", "pcmm_schoolbook", "pcmm_cussen_choose_k", "pcmm_cussen_workspace_bytes",
+    "pcmm_cussen", "pcmm_workspace_status", "pcmm_normalize", "pcmm_profile_enable",
+    "pcmm_profile_read", "pcmm_kernel_count", "pcmm_kernel_name", "pcmm_test_field", "pcmm_test_point",
 )
 
 _lock = threading.Lock()
@@ -56,6 +57,7 @@ def lib():
                 "pcmm_keytable_bytes": ([], sz),
                 "pcmm_keytable": ([u32p, vp, vp], ci),
                 "pcmm_encrypt": ([vp, vp, vp, sz, vp, vp], ci),
+                "pcmm_base_mul": ([vp, sz, vp, vp], ci),
                 "pcmm_schoolbook": ([vp, ci, ci, ci, vp, ci, vp, vp], ci),
                 "pcmm_cussen_choose_k": ([ci, ci, ci, ci], ci),
                 "pcmm_cussen_workspace_bytes": ([ci, ci, ci, ci, ci], sz),
@@ -190,6 +192,25 @@ def encrypt(table, msg, r_planar, out=None, stream=None):
     return out
 
 
+def base_mul(s_planar, count: int, out=None, stream=None):
+    """s G for count scalars (cuda int32[8 * count], quad-planar); returns
+    the affine point array, cuda int32[16 * count]."""
+    torch = _torch()
+    if out is None:
+        out = torch.empty(16 * count, dtype=torch.int32, device=s_planar.device)
+    _check(lib().pcmm_base_mul(_ptr(s_planar), count, _ptr(out), _stream(stream)), "pcmm_base_mul")
+    return out
+
+
+def public_key(sk_words: np.ndarray, device="cuda") -> np.ndarray:
+    """KeyGen on the device: H = sk G as host uint32[16] (x then y)."""
+    import torch
+    s = to_device_words(scalars_to_planar(np.asarray(sk_words, dtype=np.uint32).reshape(1, 8)), device)
+    pts = base_mul(s, 1)
+    torch.cuda.synchronize()
+    return planar_to_points(to_host_words(pts).reshape(4, 1, 4))[0]
+
+
 # ------------------------------------------------------------------ PC-MM
 
 def schoolbook(A, ctB, l: int, w: int, out=None, stream=None):
@@ -268,3 +289,28 @@ def test_point(op: int, P, Q=None, k=None, count: int = 0, stream=None):
     _check(lib().pcmm_test_point(op, _ptr(P), qp, kp, _ptr(out), count, _stream(stream)),
            "pcmm_test_point")
     return out
+
+
+# ---------------------------------------------------------------- profiler
+
+def profile_enable(capacity: int = 8192):
+    L = lib()
+    L.pcmm_profile_enable.argtypes = [ctypes.c_int]
+    L.pcmm_profile_enable.restype = ctypes.c_int
+    _check(L.pcmm_profile_enable(int(capacity)), "pcmm_profile_enable")
+
+
+def profile_read() -> dict:
+    """{kernel name: (total ms, launches)} since the last read."""
+    L = lib()
+    L.pcmm_kernel_count.restype = ctypes.c_int
+    L.pcmm_kernel_name.argtypes = [ctypes.c_int]
+    L.pcmm_kernel_name.restype = ctypes.c_char_p
+    n = int(L.pcmm_kernel_count())
+    ms = (ctypes.c_double * n)()
+    ln = (ctypes.c_longlong * n)()
+    L.pcmm_profile_read.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    L.pcmm_profile_read.restype = ctypes.c_int
+    _check(L.pcmm_profile_read(ctypes.cast(ms, ctypes.c_void_p), ctypes.cast(ln, ctypes.c_void_p)),
+           "pcmm_profile_read")
+    return {L.pcmm_kernel_name(i).decode(): (float(ms[i]), int(ln[i])) for i in range(n)}

@@ -213,3 +213,18 @@ def test_full_size_sampled(dev, w):
     sample = got[rng.integers(0, m * l, 64)]
     for ct in sample:
         assert oracle.on_curve(ct[0]) and oracle.on_curve(ct[1])
+
+
+def test_base_mul_keygen_matches_oracle(dev):
+    s = inputs.streams(123)
+    sk = inputs.uniform_scalars(s["sk"], (300,))
+    sk[0] = oracle.int_to_words(1)
+    sk[1] = oracle.int_to_words(Q - 1)
+    sk[2] = oracle.int_to_words(Q)            # = 0 mod q -> infinity
+    d = pcmm.to_device_words(pcmm.scalars_to_planar(sk), dev)
+    pts = pcmm.base_mul(d, 300)
+    torch.cuda.synchronize()
+    got = pcmm.planar_to_points(pcmm.to_host_words(pts).reshape(4, 300, 4))
+    want = oracle.base_mul(sk)
+    assert (got == want).all()
+    assert (pcmm.public_key(sk[5], device=dev) == oracle.keygen(sk[5])).all()
