@@ -47,12 +47,12 @@ __device__ __forceinline__ void warp_inverse(fe& tinv, const fe& t) {
 #pragma unroll
     for (unsigned d = 1; d < 32; d <<= 1) {
         o = fe_shfl_up(pre, d);
-        if (lane >= d) fe_mul(pre, pre, o);
+        if (lane >= d) pre = fmul(pre, o);
     }
 #pragma unroll
     for (unsigned d = 1; d < 32; d <<= 1) {
         o = fe_shfl_down(suf, d);
-        if (lane + d < 32u) fe_mul(suf, suf, o);
+        if (lane + d < 32u) suf = fmul(suf, o);
     }
     fe total = fe_shfl(pre, 31);
     fe pex = fe_shfl_up(pre, 1);    // product of lanes below
@@ -61,8 +61,8 @@ __device__ __forceinline__ void warp_inverse(fe& tinv, const fe& t) {
     if (lane == 31) fe_one(sex);
     fe inv;
     fe_inv(inv, total);
-    fe_mul(inv, inv, pex);
-    fe_mul(tinv, inv, sex);
+    inv = fmul(inv, pex);
+    tinv = fmul(inv, sex);
 }
 
 // Normalise E Jacobian points held in each lane's registers to canonical
@@ -77,7 +77,7 @@ __device__ __forceinline__ void warp_normalize_regs(aff out[E], const jac P[E]) 
     for (int e = 0; e < E; e++) {
         fe z = P[e].Z;
         if (fe_is_zero(z)) fe_one(z);
-        fe_mul(acc, acc, z);
+        acc = fmul(acc, z);
         pref[e] = acc;
     }
     fe inv;
@@ -85,12 +85,12 @@ __device__ __forceinline__ void warp_normalize_regs(aff out[E], const jac P[E]) 
 #pragma unroll
     for (int e = E - 1; e >= 0; e--) {
         fe zinv;
-        if (e > 0) fe_mul(zinv, inv, pref[e - 1]);
+        if (e > 0) zinv = fmul(inv, pref[e - 1]);
         else zinv = inv;
         fe z = P[e].Z;
         bool is_inf = fe_is_zero(z);
         if (is_inf) fe_one(z);
-        fe_mul(inv, inv, z);
+        inv = fmul(inv, z);
         if (is_inf) {
             fe_zero(out[e].x);
             fe_zero(out[e].y);

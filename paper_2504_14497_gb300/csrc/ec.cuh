@@ -3,13 +3,20 @@
 // mixed additions against affine points, and the limb-planar point layout
 // shared by every kernel.
 //
-// Formulas (Explicit-Formulas Database names, costs in field mul M and
-// squaring S):
-//   jac_dbl   "dbl-2001-b" for a = -3          3M + 5S
-//   jac_madd  "madd-2007-bl" (Z2 = 1)          7M + 4S
-//   jac_add   "add-2007-bl"                    11M + 5S
-// All three are made complete: infinity operands, P = Q (doubling) and
-// P = -Q (result infinity) are detected and handled on a rare branch.
+// Formulas (costs in field multiplications M and squarings S):
+//   jac_dbl   doubling for a = -3 ("dbl-2001-b" in the Explicit-Formulas
+//             Database)                                         3M + 5S
+//   jac_madd  textbook mixed addition: U2 = x2 Z1^2, S2 = y2 Z1^3,
+//             H = U2 - X1, R = S2 - Y1, X3 = R^2 - H^3 - 2 X1 H^2,
+//             Y3 = R (X1 H^2 - X3) - Y1 H^3, Z3 = Z1 H          8M + 3S
+//   jac_add   the same with U1 = X1 Z2^2, S1 = Y1 Z2^3,
+//             Z3 = Z1 Z2 H                                      12M + 4S
+// Y3 in both additions is a difference of two products reduced once
+// (fmulsub).  These formulas need fewer additions and subtractions than the
+// 7M + 4S / 11M + 5S variants, and additions, not multiplications, bound
+// this code on sm_103a.  All three are complete: infinity operands, P = Q
+// (doubling) and P = -Q (result infinity) are detected and handled on a rare
+// branch.
 //
 // Point arrays in global memory are QUAD-PLANAR: an array of N points stores
 // coordinate quad q (4 consecutive 32-bit limbs) of point i at uint4 index
@@ -54,36 +61,39 @@ __device__ __forceinline__ void jac_from_aff(jac& P, const aff& Q) {
     fe_one(P.Z);
 }
 
-// P <- 2P, a = -3 ("dbl-2001-b").  Infinity (Z = 0) maps to Z3 = 0.
+// P <- 2P, a = -3: delta = Z^2, gamma = Y^2, beta = X gamma,
+// alpha = 3 (X - delta)(X + delta), X3 = alpha^2 - 8 beta,
+// Z3 = (Y + Z)^2 - gamma - delta, Y3 = alpha (4 beta - X3) - 8 gamma^2.
+// Infinity (Z = 0) maps to Z3 = 0.
 __device__ __forceinline__ void jac_dbl(jac& P) {
     fe delta, gamma, beta, alpha, t0, t1;
-    fe_sqr(delta, P.Z);              // delta = Z^2
-    fe_sqr(gamma, P.Y);              // gamma = Y^2
-    fe_mul(beta, P.X, gamma);        // beta = X gamma
+    delta = fsqr(P.Z);
+    gamma = fsqr(P.Y);
+    beta = fmul(P.X, gamma);
     fe_sub(t0, P.X, delta);
     fe_add(t1, P.X, delta);
-    fe_mul(alpha, t0, t1);
+    alpha = fmul(t0, t1);
     fe_add(t0, alpha, alpha);
     fe_add(alpha, t0, alpha);        // alpha = 3 (X - delta)(X + delta)
     fe_add(t0, P.Y, P.Z);
-    fe_sqr(t0, t0);
+    t0 = fsqr(t0);
     fe_sub(t0, t0, gamma);
-    fe_sub(P.Z, t0, delta);          // Z3 = (Y + Z)^2 - gamma - delta
+    fe_sub(P.Z, t0, delta);          // Z3
     fe_add(beta, beta, beta);
     fe_add(beta, beta, beta);        // 4 beta
-    fe_sqr(t0, alpha);
+    t0 = fsqr(alpha);
     fe_sub(t0, t0, beta);
     fe_sub(P.X, t0, beta);           // X3 = alpha^2 - 8 beta
     fe_sub(t0, beta, P.X);
-    fe_mul(t0, alpha, t0);           // alpha (4 beta - X3)
-    fe_sqr(gamma, gamma);
+    t0 = fmul(alpha, t0);            // alpha (4 beta - X3)
+    gamma = fsqr(gamma);
     fe_add(gamma, gamma, gamma);
     fe_add(gamma, gamma, gamma);
     fe_add(gamma, gamma, gamma);     // 8 gamma^2
     fe_sub(P.Y, t0, gamma);          // Y3
 }
 
-// P <- P + Q for Jacobian P and affine Q ("madd-2007-bl"), complete.
+// P <- P + Q for Jacobian P and affine Q, complete.
 __device__ __forceinline__ void jac_madd(jac& P, const aff& Q) {
     if (aff_is_inf(Q)) return;
     if (jac_is_inf(P)) {
@@ -92,87 +102,63 @@ __device__ __forceinline__ void jac_madd(jac& P, const aff& Q) {
         fe_one(P.Z);
         return;
     }
-    fe z1z1, u2, s2, h, hh, i4, j, r, v, t;
-    fe_sqr(z1z1, P.Z);               // Z1Z1 = Z1^2
-    fe_mul(u2, Q.x, z1z1);           // U2 = X2 Z1Z1
-    fe_mul(s2, Q.y, P.Z);
-    fe_mul(s2, s2, z1z1);            // S2 = Y2 Z1 Z1Z1
-    fe_sub(h, u2, P.X);              // H = U2 - X1
-    fe_sub(r, s2, P.Y);
-    if (fe_is_zero(h)) {
-        if (fe_is_zero(r)) {         // same point: double
-            jac_dbl(P);
-        } else {                     // opposite points: infinity
-            jac_set_inf(P);
-        }
+    fe t1, t2, t3, t4, x3;
+    t1 = fsqr(P.Z);                  // Z1^2
+    t2 = fmul(t1, P.Z);              // Z1^3
+    t1 = fmul(t1, Q.x);              // U2
+    t2 = fmul(t2, Q.y);              // S2
+    fe_sub(t1, t1, P.X);             // H
+    fe_sub(t2, t2, P.Y);             // R
+    if (fe_is_zero(t1)) {
+        if (fe_is_zero(t2)) jac_dbl(P);   // same point
+        else jac_set_inf(P);              // opposite points
         return;
     }
-    fe_add(r, r, r);                 // r = 2 (S2 - Y1)
-    fe_sqr(hh, h);                   // HH = H^2
-    fe_add(i4, hh, hh);
-    fe_add(i4, i4, i4);              // I = 4 HH
-    fe_mul(j, h, i4);                // J = H I
-    fe_mul(v, P.X, i4);              // V = X1 I
-    fe_add(t, P.Z, h);
-    fe_sqr(t, t);
-    fe_sub(t, t, z1z1);
-    fe_sub(P.Z, t, hh);              // Z3 = (Z1 + H)^2 - Z1Z1 - HH
-    fe_sqr(t, r);
-    fe_sub(t, t, j);
-    fe_sub(t, t, v);
-    fe_sub(P.X, t, v);               // X3 = r^2 - J - 2V
-    fe_sub(t, v, P.X);
-    fe_mul(t, r, t);                 // r (V - X3)
-    fe_mul(j, P.Y, j);
-    fe_add(j, j, j);                 // 2 Y1 J
-    fe_sub(P.Y, t, j);               // Y3
+    P.Z = fmul(P.Z, t1);             // Z3 = Z1 H
+    t4 = fsqr(t1);                   // H^2
+    t3 = fmul(t4, t1);               // H^3
+    t4 = fmul(t4, P.X);              // X1 H^2
+    fe_add(t1, t4, t4);              // 2 X1 H^2
+    x3 = fsqr(t2);                   // R^2
+    fe_sub(x3, x3, t1);
+    fe_sub(x3, x3, t3);              // X3 = R^2 - 2 X1 H^2 - H^3
+    fe_sub(t4, t4, x3);              // X1 H^2 - X3
+    P.Y = fmulsub(t4, t2, t3, P.Y);  // Y3 = R (X1 H^2 - X3) - Y1 H^3
+    P.X = x3;
 }
 
-// P <- P + Q, both Jacobian ("add-2007-bl"), complete.
+// P <- P + Q, both Jacobian, complete.
 __device__ __forceinline__ void jac_add(jac& P, const jac& Q) {
     if (jac_is_inf(Q)) return;
     if (jac_is_inf(P)) {
         P = Q;
         return;
     }
-    fe z1z1, z2z2, u1, u2, s1, s2, h, i, j, r, v, t;
-    fe_sqr(z1z1, P.Z);
-    fe_sqr(z2z2, Q.Z);
-    fe_mul(u1, P.X, z2z2);           // U1 = X1 Z2Z2
-    fe_mul(u2, Q.X, z1z1);           // U2 = X2 Z1Z1
-    fe_mul(s1, P.Y, Q.Z);
-    fe_mul(s1, s1, z2z2);            // S1 = Y1 Z2 Z2Z2
-    fe_mul(s2, Q.Y, P.Z);
-    fe_mul(s2, s2, z1z1);            // S2 = Y2 Z1 Z1Z1
-    fe_sub(h, u2, u1);               // H = U2 - U1
-    fe_sub(r, s2, s1);
+    fe z1z1, z2z2, u1, u2, s1, s2, h, r, t3, t4, x3;
+    z1z1 = fsqr(P.Z);
+    z2z2 = fsqr(Q.Z);
+    u1 = fmul(P.X, z2z2);            // U1 = X1 Z2^2
+    u2 = fmul(Q.X, z1z1);            // U2 = X2 Z1^2
+    s1 = fmul(P.Y, fmul(z2z2, Q.Z)); // S1 = Y1 Z2^3
+    s2 = fmul(Q.Y, fmul(z1z1, P.Z)); // S2 = Y2 Z1^3
+    fe_sub(h, u2, u1);               // H
+    fe_sub(r, s2, s1);               // R
     if (fe_is_zero(h)) {
-        if (fe_is_zero(r)) {
-            jac_dbl(P);
-        } else {
-            jac_set_inf(P);
-        }
+        if (fe_is_zero(r)) jac_dbl(P);
+        else jac_set_inf(P);
         return;
     }
-    fe_add(r, r, r);                 // r = 2 (S2 - S1)
-    fe_add(i, h, h);
-    fe_sqr(i, i);                    // I = (2H)^2
-    fe_mul(j, h, i);                 // J = H I
-    fe_mul(v, u1, i);                // V = U1 I
-    fe_add(t, P.Z, Q.Z);
-    fe_sqr(t, t);
-    fe_sub(t, t, z1z1);
-    fe_sub(t, t, z2z2);
-    fe_mul(P.Z, t, h);               // Z3 = ((Z1 + Z2)^2 - Z1Z1 - Z2Z2) H
-    fe_sqr(t, r);
-    fe_sub(t, t, j);
-    fe_sub(t, t, v);
-    fe_sub(P.X, t, v);               // X3 = r^2 - J - 2V
-    fe_sub(t, v, P.X);
-    fe_mul(t, r, t);
-    fe_mul(s1, s1, j);
-    fe_add(s1, s1, s1);              // 2 S1 J
-    fe_sub(P.Y, t, s1);              // Y3
+    P.Z = fmul(fmul(P.Z, Q.Z), h);   // Z3 = Z1 Z2 H
+    t4 = fsqr(h);                    // H^2
+    t3 = fmul(t4, h);                // H^3
+    t4 = fmul(t4, u1);               // U1 H^2
+    fe_add(u2, t4, t4);              // 2 U1 H^2
+    x3 = fsqr(r);
+    fe_sub(x3, x3, u2);
+    fe_sub(x3, x3, t3);              // X3 = R^2 - 2 U1 H^2 - H^3
+    fe_sub(t4, t4, x3);              // U1 H^2 - X3
+    P.Y = fmulsub(t4, r, t3, s1);    // Y3 = R (U1 H^2 - X3) - S1 H^3
+    P.X = x3;
 }
 
 // P <- k P for a small non-negative scalar k (at most 32 bits) by
@@ -241,11 +227,10 @@ __device__ __forceinline__ void store_fe(uint4* __restrict__ base, size_t stride
 
 // Affine from Jacobian given zinv = Z^-1 (Z != 0); canonical output.
 __device__ __forceinline__ void jac_to_aff_with_zinv(aff& Q, const jac& P, const fe& zinv) {
-    fe z2, z3;
-    fe_sqr(z2, zinv);
-    fe_mul(z3, z2, zinv);
-    fe_mul(Q.x, P.X, z2);
-    fe_mul(Q.y, P.Y, z3);
+    fe z2 = fsqr(zinv);
+    fe z3 = fmul(z2, zinv);
+    Q.x = fmul(P.X, z2);
+    Q.y = fmul(P.Y, z3);
     fe_canon(Q.x, Q.x);
     fe_canon(Q.y, Q.y);
 }

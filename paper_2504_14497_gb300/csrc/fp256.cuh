@@ -7,9 +7,16 @@
 // representative below p; it is applied only when a result leaves the
 // library or when a value must be compared.
 //
-// Multiplication: 8x8-limb operand scanning with mad.lo/madc.hi carry chains
-// (64 limb products = 128 IMAD); squaring: 28 cross products doubled plus 8
-// diagonal squares (72 IMAD).  Reduction of the 512-bit product uses the
+// Multiplication: 8x8-limb operand scanning, one row per limb of b.  Each
+// limb product is a single 32x32->64-bit multiply-add (mad.wide.u32, which
+// also adds the row's running word), and the high halves are folded in with
+// one add-with-carry chain per row: 64 wide products and 64 carry adds.
+// (On sm_103a a wide multiply-add costs as much as a high-half multiply, and
+// twice a low-half multiply, so separate lo/hi products would cost 1.5x.)
+// Squaring: 28 cross products, doubled, plus 8 diagonal squares.  Products
+// and reductions live in out-of-line functions (fmul, fsqr): inlining them
+// into every call site of a point formula overflows the instruction cache.
+// Reduction of the 512-bit product uses the
 // special form of p (Solinas, FIPS 186-4 D.2): with 2^256 = 2^224 - 2^192 -
 // 2^96 + 1 (mod p), the product c = (c15..c0) reduces to
 //     T + 2 S1 + 2 S2 + S3 + S4 - D1 - D2 - D3 - D4       (mod p)
@@ -78,8 +85,9 @@ __device__ __forceinline__ uint32_t fe_sub_K_masked(fe& r, uint32_t mask) {
     return b & 1u;
 }
 
-// r = a + b mod p (weak).  a + b < 2^257; each carry out of 2^256 is
-// replaced by adding K; at most two folds are needed.
+// r = a + b mod p (weak).  a + b < 2^257; a carry out of 2^256 is replaced by
+// adding K = 2^256 mod p.  A second carry (only when the first fold lands at
+// or above 2^256, probability about 2^-32) takes a branch.
 __device__ __forceinline__ void fe_add(fe& r, const fe& a, const fe& b) {
     uint32_t c;
     asm("add.cc.u32  %0, %9, %17;\n\t"
@@ -97,12 +105,12 @@ __device__ __forceinline__ void fe_add(fe& r, const fe& a, const fe& b) {
           "r"(a.v[6]), "r"(a.v[7]), "r"(b.v[0]), "r"(b.v[1]), "r"(b.v[2]), "r"(b.v[3]),
           "r"(b.v[4]), "r"(b.v[5]), "r"(b.v[6]), "r"(b.v[7]));
     c = fe_add_K_masked(r, 0u - c);
-    fe_add_K_masked(r, 0u - c);
+    if (c) fe_add_K_masked(r, 0xffffffffu);
 }
 
 // r = a - b mod p (weak).  A borrow means the register holds a - b + 2^256;
-// subtracting K turns that into a - b + p; a second borrow (b - a > p)
-// subtracts K again, giving a - b + 2p.
+// subtracting K turns that into a - b + p; a second borrow (only if b - a > p,
+// which needs a weakly reduced b >= p) subtracts K again on a branch.
 __device__ __forceinline__ void fe_sub(fe& r, const fe& a, const fe& b) {
     uint32_t bw;
     asm("sub.cc.u32  %0, %9, %17;\n\t"
@@ -119,8 +127,8 @@ __device__ __forceinline__ void fe_sub(fe& r, const fe& a, const fe& b) {
         : "r"(a.v[0]), "r"(a.v[1]), "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]),
           "r"(a.v[6]), "r"(a.v[7]), "r"(b.v[0]), "r"(b.v[1]), "r"(b.v[2]), "r"(b.v[3]),
           "r"(b.v[4]), "r"(b.v[5]), "r"(b.v[6]), "r"(b.v[7]));
-    bw = fe_sub_K_masked(r, bw);  // bw is 0 or 0xffffffff
-    fe_sub_K_masked(r, 0u - bw);
+    bw = fe_sub_K_masked(r, bw);
+    if (bw) fe_sub_K_masked(r, 0xffffffffu);
 }
 
 __device__ __forceinline__ void fe_dbl(fe& r, const fe& a) { fe_add(r, a, a); }
@@ -304,153 +312,144 @@ __device__ __forceinline__ void fe_reduce(fe& r, const uint32_t c[16]) {
           "=r"(b1)
         : "r"(a8));
     // The folded value is non-negative and below 2^256 + 11 * 2^224, so the
-    // net top word e1 + b1 (b1 is 0 or -1) is 0 or 1; one more fold suffices.
+    // net top word e1 + b1 (b1 is 0 or -1) is 0 or 1; it is 1 only when the
+    // value reached 2^256 (probability below 2^-27), handled on a branch.
     r.v[0] = a0; r.v[1] = a1; r.v[2] = a2; r.v[3] = a3;
     r.v[4] = a4; r.v[5] = a5; r.v[6] = a6; r.v[7] = a7;
-    fe_add_K_masked(r, 0u - (e1 + b1));
+    if (e1 + b1) fe_add_K_masked(r, 0xffffffffu);
 }
 
-// t[0..15] = a * b, operand scanning, one carry chain pair per row.
+// t[0..15] = a * b.  Row i: p_j = a_j b_i + t[i+j] (one wide multiply-add,
+// never overflowing 64 bits), t[i] = lo(p_0), t[i+j] = lo(p_j) + hi(p_j-1)
+// + carry, t[i+8] = hi(p_7) + carry.
 __device__ __forceinline__ void mul_wide(uint32_t t[16], const fe& a, const fe& b) {
-    // Row 0.
-    asm("mul.lo.u32     %0, %9, %17;\n\t"
-        "mul.lo.u32     %1, %10, %17;\n\t"
-        "mul.lo.u32     %2, %11, %17;\n\t"
-        "mul.lo.u32     %3, %12, %17;\n\t"
-        "mul.lo.u32     %4, %13, %17;\n\t"
-        "mul.lo.u32     %5, %14, %17;\n\t"
-        "mul.lo.u32     %6, %15, %17;\n\t"
-        "mul.lo.u32     %7, %16, %17;\n\t"
-        "mad.hi.cc.u32  %1, %9, %17, %1;\n\t"
-        "madc.hi.cc.u32 %2, %10, %17, %2;\n\t"
-        "madc.hi.cc.u32 %3, %11, %17, %3;\n\t"
-        "madc.hi.cc.u32 %4, %12, %17, %4;\n\t"
-        "madc.hi.cc.u32 %5, %13, %17, %5;\n\t"
-        "madc.hi.cc.u32 %6, %14, %17, %6;\n\t"
-        "madc.hi.cc.u32 %7, %15, %17, %7;\n\t"
-        "madc.hi.u32    %8, %16, %17, 0;"
-        : "=r"(t[0]), "=r"(t[1]), "=r"(t[2]), "=r"(t[3]), "=r"(t[4]), "=r"(t[5]), "=r"(t[6]),
-          "=r"(t[7]), "=r"(t[8])
-        : "r"(a.v[0]), "r"(a.v[1]), "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]),
-          "r"(a.v[6]), "r"(a.v[7]), "r"(b.v[0]));
-    // Rows 1..7: t[i..i+7] += lo(a b_i), carry into the new word t[i+8],
-    // then t[i+1..i+8] += hi(a b_i).  The partial sum is below 2^(32(i+9)),
-    // so the final hi chain cannot carry out.
+    uint64_t p[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) p[j] = (uint64_t)a.v[j] * b.v[0];
+    t[0] = (uint32_t)p[0];
+    asm("add.cc.u32 %0, %8, %15;\n\taddc.cc.u32 %1, %9, %16;\n\taddc.cc.u32 %2, %10, %17;\n\t"
+        "addc.cc.u32 %3, %11, %18;\n\taddc.cc.u32 %4, %12, %19;\n\taddc.cc.u32 %5, %13, %20;\n\t"
+        "addc.cc.u32 %6, %14, %21;\n\taddc.u32 %7, %22, 0;"
+        : "=r"(t[1]), "=r"(t[2]), "=r"(t[3]), "=r"(t[4]), "=r"(t[5]), "=r"(t[6]), "=r"(t[7]), "=r"(t[8])
+        : "r"((uint32_t)p[1]), "r"((uint32_t)p[2]), "r"((uint32_t)p[3]), "r"((uint32_t)p[4]), "r"((uint32_t)p[5]),
+          "r"((uint32_t)p[6]), "r"((uint32_t)p[7]), "r"((uint32_t)(p[0] >> 32)), "r"((uint32_t)(p[1] >> 32)),
+          "r"((uint32_t)(p[2] >> 32)), "r"((uint32_t)(p[3] >> 32)), "r"((uint32_t)(p[4] >> 32)),
+          "r"((uint32_t)(p[5] >> 32)), "r"((uint32_t)(p[6] >> 32)), "r"((uint32_t)(p[7] >> 32)));
 #pragma unroll
     for (int i = 1; i < 8; i++) {
-        asm("mad.lo.cc.u32  %0, %9, %17, %0;\n\t"
-            "madc.lo.cc.u32 %1, %10, %17, %1;\n\t"
-            "madc.lo.cc.u32 %2, %11, %17, %2;\n\t"
-            "madc.lo.cc.u32 %3, %12, %17, %3;\n\t"
-            "madc.lo.cc.u32 %4, %13, %17, %4;\n\t"
-            "madc.lo.cc.u32 %5, %14, %17, %5;\n\t"
-            "madc.lo.cc.u32 %6, %15, %17, %6;\n\t"
-            "madc.lo.cc.u32 %7, %16, %17, %7;\n\t"
-            "addc.u32       %8, 0, 0;\n\t"
-            "mad.hi.cc.u32  %1, %9, %17, %1;\n\t"
-            "madc.hi.cc.u32 %2, %10, %17, %2;\n\t"
-            "madc.hi.cc.u32 %3, %11, %17, %3;\n\t"
-            "madc.hi.cc.u32 %4, %12, %17, %4;\n\t"
-            "madc.hi.cc.u32 %5, %13, %17, %5;\n\t"
-            "madc.hi.cc.u32 %6, %14, %17, %6;\n\t"
-            "madc.hi.cc.u32 %7, %15, %17, %7;\n\t"
-            "madc.hi.u32    %8, %16, %17, %8;"
-            : "+r"(t[i]), "+r"(t[i + 1]), "+r"(t[i + 2]), "+r"(t[i + 3]), "+r"(t[i + 4]),
-              "+r"(t[i + 5]), "+r"(t[i + 6]), "+r"(t[i + 7]), "=r"(t[i + 8])
-            : "r"(a.v[0]), "r"(a.v[1]), "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]),
-              "r"(a.v[6]), "r"(a.v[7]), "r"(b.v[i]));
+#pragma unroll
+        for (int j = 0; j < 8; j++) p[j] = (uint64_t)a.v[j] * b.v[i] + t[i + j];
+        t[i] = (uint32_t)p[0];
+        asm("add.cc.u32 %0, %8, %15;\n\taddc.cc.u32 %1, %9, %16;\n\taddc.cc.u32 %2, %10, %17;\n\t"
+            "addc.cc.u32 %3, %11, %18;\n\taddc.cc.u32 %4, %12, %19;\n\taddc.cc.u32 %5, %13, %20;\n\t"
+            "addc.cc.u32 %6, %14, %21;\n\taddc.u32 %7, %22, 0;"
+            : "=r"(t[i + 1]), "=r"(t[i + 2]), "=r"(t[i + 3]), "=r"(t[i + 4]), "=r"(t[i + 5]), "=r"(t[i + 6]),
+              "=r"(t[i + 7]), "=r"(t[i + 8])
+            : "r"((uint32_t)p[1]), "r"((uint32_t)p[2]), "r"((uint32_t)p[3]), "r"((uint32_t)p[4]), "r"((uint32_t)p[5]),
+              "r"((uint32_t)p[6]), "r"((uint32_t)p[7]), "r"((uint32_t)(p[0] >> 32)), "r"((uint32_t)(p[1] >> 32)),
+              "r"((uint32_t)(p[2] >> 32)), "r"((uint32_t)(p[3] >> 32)), "r"((uint32_t)(p[4] >> 32)),
+              "r"((uint32_t)(p[5] >> 32)), "r"((uint32_t)(p[6] >> 32)), "r"((uint32_t)(p[7] >> 32)));
     }
 }
 
-// t[0..15] = a^2: cross products a_i a_j (i < j) doubled, plus the squares.
+// out[k] = lo[k] + hi[k] + carry (k < N), out[N] = hi[N] + carry: one carry
+// chain, kept inside a single asm statement so the carry flag survives.
+template <int N> __device__ __forceinline__ void chain_add(uint32_t* out, const uint32_t* lo, const uint32_t* hi);
+template <> __device__ __forceinline__ void chain_add<1>(uint32_t* out, const uint32_t* lo, const uint32_t* hi) {
+    asm("add.cc.u32  %0, %2, %3;\n\t"
+        "addc.u32 %1, %4, 0;"
+        : "=r"(out[0]), "=r"(out[1])
+        : "r"(lo[0]), "r"(hi[0]), "r"(hi[1]));
+}
+template <> __device__ __forceinline__ void chain_add<2>(uint32_t* out, const uint32_t* lo, const uint32_t* hi) {
+    asm("add.cc.u32  %0, %3, %5;\n\t"
+        "addc.cc.u32 %1, %4, %6;\n\t"
+        "addc.u32 %2, %7, 0;"
+        : "=r"(out[0]), "=r"(out[1]), "=r"(out[2])
+        : "r"(lo[0]), "r"(lo[1]), "r"(hi[0]), "r"(hi[1]), "r"(hi[2]));
+}
+template <> __device__ __forceinline__ void chain_add<3>(uint32_t* out, const uint32_t* lo, const uint32_t* hi) {
+    asm("add.cc.u32  %0, %4, %7;\n\t"
+        "addc.cc.u32 %1, %5, %8;\n\t"
+        "addc.cc.u32 %2, %6, %9;\n\t"
+        "addc.u32 %3, %10, 0;"
+        : "=r"(out[0]), "=r"(out[1]), "=r"(out[2]), "=r"(out[3])
+        : "r"(lo[0]), "r"(lo[1]), "r"(lo[2]), "r"(hi[0]), "r"(hi[1]), "r"(hi[2]), "r"(hi[3]));
+}
+template <> __device__ __forceinline__ void chain_add<4>(uint32_t* out, const uint32_t* lo, const uint32_t* hi) {
+    asm("add.cc.u32  %0, %5, %9;\n\t"
+        "addc.cc.u32 %1, %6, %10;\n\t"
+        "addc.cc.u32 %2, %7, %11;\n\t"
+        "addc.cc.u32 %3, %8, %12;\n\t"
+        "addc.u32 %4, %13, 0;"
+        : "=r"(out[0]), "=r"(out[1]), "=r"(out[2]), "=r"(out[3]), "=r"(out[4])
+        : "r"(lo[0]), "r"(lo[1]), "r"(lo[2]), "r"(lo[3]), "r"(hi[0]), "r"(hi[1]), "r"(hi[2]), "r"(hi[3]), "r"(hi[4]));
+}
+template <> __device__ __forceinline__ void chain_add<5>(uint32_t* out, const uint32_t* lo, const uint32_t* hi) {
+    asm("add.cc.u32  %0, %6, %11;\n\t"
+        "addc.cc.u32 %1, %7, %12;\n\t"
+        "addc.cc.u32 %2, %8, %13;\n\t"
+        "addc.cc.u32 %3, %9, %14;\n\t"
+        "addc.cc.u32 %4, %10, %15;\n\t"
+        "addc.u32 %5, %16, 0;"
+        : "=r"(out[0]), "=r"(out[1]), "=r"(out[2]), "=r"(out[3]), "=r"(out[4]), "=r"(out[5])
+        : "r"(lo[0]), "r"(lo[1]), "r"(lo[2]), "r"(lo[3]), "r"(lo[4]), "r"(hi[0]), "r"(hi[1]), "r"(hi[2]), "r"(hi[3]), "r"(hi[4]), "r"(hi[5]));
+}
+template <> __device__ __forceinline__ void chain_add<6>(uint32_t* out, const uint32_t* lo, const uint32_t* hi) {
+    asm("add.cc.u32  %0, %7, %13;\n\t"
+        "addc.cc.u32 %1, %8, %14;\n\t"
+        "addc.cc.u32 %2, %9, %15;\n\t"
+        "addc.cc.u32 %3, %10, %16;\n\t"
+        "addc.cc.u32 %4, %11, %17;\n\t"
+        "addc.cc.u32 %5, %12, %18;\n\t"
+        "addc.u32 %6, %19, 0;"
+        : "=r"(out[0]), "=r"(out[1]), "=r"(out[2]), "=r"(out[3]), "=r"(out[4]), "=r"(out[5]), "=r"(out[6])
+        : "r"(lo[0]), "r"(lo[1]), "r"(lo[2]), "r"(lo[3]), "r"(lo[4]), "r"(lo[5]), "r"(hi[0]), "r"(hi[1]), "r"(hi[2]), "r"(hi[3]), "r"(hi[4]), "r"(hi[5]), "r"(hi[6]));
+}
+template <> __device__ __forceinline__ void chain_add<7>(uint32_t* out, const uint32_t* lo, const uint32_t* hi) {
+    asm("add.cc.u32  %0, %8, %15;\n\t"
+        "addc.cc.u32 %1, %9, %16;\n\t"
+        "addc.cc.u32 %2, %10, %17;\n\t"
+        "addc.cc.u32 %3, %11, %18;\n\t"
+        "addc.cc.u32 %4, %12, %19;\n\t"
+        "addc.cc.u32 %5, %13, %20;\n\t"
+        "addc.cc.u32 %6, %14, %21;\n\t"
+        "addc.u32 %7, %22, 0;"
+        : "=r"(out[0]), "=r"(out[1]), "=r"(out[2]), "=r"(out[3]), "=r"(out[4]), "=r"(out[5]), "=r"(out[6]), "=r"(out[7])
+        : "r"(lo[0]), "r"(lo[1]), "r"(lo[2]), "r"(lo[3]), "r"(lo[4]), "r"(lo[5]), "r"(lo[6]), "r"(hi[0]), "r"(hi[1]), "r"(hi[2]), "r"(hi[3]), "r"(hi[4]), "r"(hi[5]), "r"(hi[6]), "r"(hi[7]));
+}
+
+// Squaring with wide products: cross products row by row, doubled, plus squares.
 __device__ __forceinline__ void sqr_wide(uint32_t t[16], const fe& a) {
-    // Cross products into t[1..14]; t[0] = t[15] = 0 for now.
-    // Row 0: a0 * a1..a7 at words 1..8.
-    asm("mul.lo.u32     %0, %8, %9;\n\t"
-        "mul.lo.u32     %1, %8, %10;\n\t"
-        "mul.lo.u32     %2, %8, %11;\n\t"
-        "mul.lo.u32     %3, %8, %12;\n\t"
-        "mul.lo.u32     %4, %8, %13;\n\t"
-        "mul.lo.u32     %5, %8, %14;\n\t"
-        "mul.lo.u32     %6, %8, %15;\n\t"
-        "mad.hi.cc.u32  %1, %8, %9, %1;\n\t"
-        "madc.hi.cc.u32 %2, %8, %10, %2;\n\t"
-        "madc.hi.cc.u32 %3, %8, %11, %3;\n\t"
-        "madc.hi.cc.u32 %4, %8, %12, %4;\n\t"
-        "madc.hi.cc.u32 %5, %8, %13, %5;\n\t"
-        "madc.hi.cc.u32 %6, %8, %14, %6;\n\t"
-        "madc.hi.u32    %7, %8, %15, 0;"
-        : "=r"(t[1]), "=r"(t[2]), "=r"(t[3]), "=r"(t[4]), "=r"(t[5]), "=r"(t[6]), "=r"(t[7]),
-          "=r"(t[8])
-        : "r"(a.v[0]), "r"(a.v[1]), "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]),
-          "r"(a.v[6]), "r"(a.v[7]));
-    // Row 1: a1 * a2..a7 at words 3..9.
-    asm("mad.lo.cc.u32  %0, %7, %8, %0;\n\t"
-        "madc.lo.cc.u32 %1, %7, %9, %1;\n\t"
-        "madc.lo.cc.u32 %2, %7, %10, %2;\n\t"
-        "madc.lo.cc.u32 %3, %7, %11, %3;\n\t"
-        "madc.lo.cc.u32 %4, %7, %12, %4;\n\t"
-        "madc.lo.cc.u32 %5, %7, %13, %5;\n\t"
-        "addc.u32       %6, 0, 0;\n\t"
-        "mad.hi.cc.u32  %1, %7, %8, %1;\n\t"
-        "madc.hi.cc.u32 %2, %7, %9, %2;\n\t"
-        "madc.hi.cc.u32 %3, %7, %10, %3;\n\t"
-        "madc.hi.cc.u32 %4, %7, %11, %4;\n\t"
-        "madc.hi.cc.u32 %5, %7, %12, %5;\n\t"
-        "madc.hi.u32    %6, %7, %13, %6;"
-        : "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "+r"(t[8]), "=r"(t[9])
-        : "r"(a.v[1]), "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]), "r"(a.v[6]),
-          "r"(a.v[7]));
-    // Row 2: a2 * a3..a7 at words 5..10.
-    asm("mad.lo.cc.u32  %0, %6, %7, %0;\n\t"
-        "madc.lo.cc.u32 %1, %6, %8, %1;\n\t"
-        "madc.lo.cc.u32 %2, %6, %9, %2;\n\t"
-        "madc.lo.cc.u32 %3, %6, %10, %3;\n\t"
-        "madc.lo.cc.u32 %4, %6, %11, %4;\n\t"
-        "addc.u32       %5, 0, 0;\n\t"
-        "mad.hi.cc.u32  %1, %6, %7, %1;\n\t"
-        "madc.hi.cc.u32 %2, %6, %8, %2;\n\t"
-        "madc.hi.cc.u32 %3, %6, %9, %3;\n\t"
-        "madc.hi.cc.u32 %4, %6, %10, %4;\n\t"
-        "madc.hi.u32    %5, %6, %11, %5;"
-        : "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "+r"(t[8]), "+r"(t[9]), "=r"(t[10])
-        : "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]), "r"(a.v[6]), "r"(a.v[7]));
-    // Row 3: a3 * a4..a7 at words 7..11.
-    asm("mad.lo.cc.u32  %0, %5, %6, %0;\n\t"
-        "madc.lo.cc.u32 %1, %5, %7, %1;\n\t"
-        "madc.lo.cc.u32 %2, %5, %8, %2;\n\t"
-        "madc.lo.cc.u32 %3, %5, %9, %3;\n\t"
-        "addc.u32       %4, 0, 0;\n\t"
-        "mad.hi.cc.u32  %1, %5, %6, %1;\n\t"
-        "madc.hi.cc.u32 %2, %5, %7, %2;\n\t"
-        "madc.hi.cc.u32 %3, %5, %8, %3;\n\t"
-        "madc.hi.u32    %4, %5, %9, %4;"
-        : "+r"(t[7]), "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "=r"(t[11])
-        : "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]), "r"(a.v[6]), "r"(a.v[7]));
-    // Row 4: a4 * a5..a7 at words 9..12.
-    asm("mad.lo.cc.u32  %0, %4, %5, %0;\n\t"
-        "madc.lo.cc.u32 %1, %4, %6, %1;\n\t"
-        "madc.lo.cc.u32 %2, %4, %7, %2;\n\t"
-        "addc.u32       %3, 0, 0;\n\t"
-        "mad.hi.cc.u32  %1, %4, %5, %1;\n\t"
-        "madc.hi.cc.u32 %2, %4, %6, %2;\n\t"
-        "madc.hi.u32    %3, %4, %7, %3;"
-        : "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "=r"(t[12])
-        : "r"(a.v[4]), "r"(a.v[5]), "r"(a.v[6]), "r"(a.v[7]));
-    // Row 5: a5 * a6..a7 at words 11..13.
-    asm("mad.lo.cc.u32  %0, %3, %4, %0;\n\t"
-        "madc.lo.cc.u32 %1, %3, %5, %1;\n\t"
-        "addc.u32       %2, 0, 0;\n\t"
-        "mad.hi.cc.u32  %1, %3, %4, %1;\n\t"
-        "madc.hi.u32    %2, %3, %5, %2;"
-        : "+r"(t[11]), "+r"(t[12]), "=r"(t[13])
-        : "r"(a.v[5]), "r"(a.v[6]), "r"(a.v[7]));
-    // Row 6: a6 * a7 at words 13..14.
-    asm("mad.lo.cc.u32  %0, %2, %3, %0;\n\t"
-        "madc.hi.u32    %1, %2, %3, 0;"
-        : "+r"(t[13]), "=r"(t[14])
-        : "r"(a.v[6]), "r"(a.v[7]));
-    // Double the cross products and add the diagonal squares a_i^2 at 2i.
+    uint32_t lo[8], hi[8];
+    // row 0: a0 * a1..a7 -> t[1..8]
+#pragma unroll
+    for (int j = 1; j < 8; j++) {
+        uint64_t p = (uint64_t)a.v[0] * a.v[j];
+        lo[j] = (uint32_t)p; hi[j] = (uint32_t)(p >> 32);
+    }
+    t[1] = lo[1];
+    chain_add<6>(&t[2], &lo[2], &hi[1]);
+#define SQROW(I)                                                        \
+    {                                                                   \
+        _Pragma("unroll") for (int j = I + 1; j < 8; j++) {             \
+            uint64_t p = (uint64_t)a.v[I] * a.v[j] + t[I + j];          \
+            lo[j] = (uint32_t)p; hi[j] = (uint32_t)(p >> 32);           \
+        }                                                               \
+        t[2 * I + 1] = lo[I + 1];                                       \
+        chain_add<6 - I>(&t[2 * I + 2], &lo[I + 2], &hi[I + 1]);        \
+    }
+    SQROW(1) SQROW(2) SQROW(3) SQROW(4) SQROW(5)
+#undef SQROW
+    {
+        uint64_t p = (uint64_t)a.v[6] * a.v[7] + t[13];
+        t[13] = (uint32_t)p;
+        t[14] = (uint32_t)(p >> 32);
+    }
+    // double u[1..14] and add the squares a_i^2 at 2i
+    uint64_t d[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) d[i] = (uint64_t)a.v[i] * a.v[i];
     asm("add.cc.u32  %1, %1, %1;\n\t"
         "addc.cc.u32 %2, %2, %2;\n\t"
         "addc.cc.u32 %3, %3, %3;\n\t"
@@ -466,27 +465,28 @@ __device__ __forceinline__ void sqr_wide(uint32_t t[16], const fe& a) {
         "addc.cc.u32 %13, %13, %13;\n\t"
         "addc.cc.u32 %14, %14, %14;\n\t"
         "addc.u32    %15, 0, 0;\n\t"
-        "mul.lo.u32     %0, %16, %16;\n\t"
-        "mad.hi.cc.u32  %1, %16, %16, %1;\n\t"
-        "madc.lo.cc.u32 %2, %17, %17, %2;\n\t"
-        "madc.hi.cc.u32 %3, %17, %17, %3;\n\t"
-        "madc.lo.cc.u32 %4, %18, %18, %4;\n\t"
-        "madc.hi.cc.u32 %5, %18, %18, %5;\n\t"
-        "madc.lo.cc.u32 %6, %19, %19, %6;\n\t"
-        "madc.hi.cc.u32 %7, %19, %19, %7;\n\t"
-        "madc.lo.cc.u32 %8, %20, %20, %8;\n\t"
-        "madc.hi.cc.u32 %9, %20, %20, %9;\n\t"
-        "madc.lo.cc.u32 %10, %21, %21, %10;\n\t"
-        "madc.hi.cc.u32 %11, %21, %21, %11;\n\t"
-        "madc.lo.cc.u32 %12, %22, %22, %12;\n\t"
-        "madc.hi.cc.u32 %13, %22, %22, %13;\n\t"
-        "madc.lo.cc.u32 %14, %23, %23, %14;\n\t"
-        "madc.hi.u32    %15, %23, %23, %15;"
-        : "=r"(t[0]), "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]),
-          "+r"(t[7]), "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12]),
-          "+r"(t[13]), "+r"(t[14]), "=r"(t[15])
-        : "r"(a.v[0]), "r"(a.v[1]), "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]),
-          "r"(a.v[6]), "r"(a.v[7]));
+        "mov.b32     %0, %16;\n\t"
+        "add.cc.u32  %1, %1, %17;\n\t"
+        "addc.cc.u32 %2, %2, %18;\n\t"
+        "addc.cc.u32 %3, %3, %19;\n\t"
+        "addc.cc.u32 %4, %4, %20;\n\t"
+        "addc.cc.u32 %5, %5, %21;\n\t"
+        "addc.cc.u32 %6, %6, %22;\n\t"
+        "addc.cc.u32 %7, %7, %23;\n\t"
+        "addc.cc.u32 %8, %8, %24;\n\t"
+        "addc.cc.u32 %9, %9, %25;\n\t"
+        "addc.cc.u32 %10, %10, %26;\n\t"
+        "addc.cc.u32 %11, %11, %27;\n\t"
+        "addc.cc.u32 %12, %12, %28;\n\t"
+        "addc.cc.u32 %13, %13, %29;\n\t"
+        "addc.cc.u32 %14, %14, %30;\n\t"
+        "addc.u32    %15, %15, %31;"
+        : "=r"(t[0]), "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]),
+          "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12]), "+r"(t[13]), "+r"(t[14]), "=r"(t[15])
+        : "r"((uint32_t)d[0]), "r"((uint32_t)(d[0] >> 32)), "r"((uint32_t)d[1]), "r"((uint32_t)(d[1] >> 32)),
+          "r"((uint32_t)d[2]), "r"((uint32_t)(d[2] >> 32)), "r"((uint32_t)d[3]), "r"((uint32_t)(d[3] >> 32)),
+          "r"((uint32_t)d[4]), "r"((uint32_t)(d[4] >> 32)), "r"((uint32_t)d[5]), "r"((uint32_t)(d[5] >> 32)),
+          "r"((uint32_t)d[6]), "r"((uint32_t)(d[6] >> 32)), "r"((uint32_t)d[7]), "r"((uint32_t)(d[7] >> 32)));
 }
 
 __device__ __forceinline__ void fe_mul(fe& r, const fe& a, const fe& b) {
@@ -501,9 +501,24 @@ __device__ __forceinline__ void fe_sqr(fe& r, const fe& a) {
     fe_reduce(r, t);
 }
 
-__device__ __forceinline__ void fe_sqr_n(fe& r, const fe& a, int n) {
+// Out-of-line multiplication and squaring (by value): the hot point formulas
+// call these so that one copy of the product and reduction code serves every
+// call site.
+static __device__ __noinline__ fe fmul(fe a, fe b) {
+    fe r;
+    fe_mul(r, a, b);
+    return r;
+}
+
+static __device__ __noinline__ fe fsqr(fe a) {
+    fe r;
     fe_sqr(r, a);
-    for (int i = 1; i < n; i++) fe_sqr(r, r);
+    return r;
+}
+
+__device__ __forceinline__ void fe_sqr_n(fe& r, const fe& a, int n) {
+    r = fsqr(a);
+    for (int i = 1; i < n; i++) r = fsqr(r);
 }
 
 // r = a^(p-2) = a^-1 for a != 0 (Fermat).  Addition chain over the runs of
@@ -512,24 +527,84 @@ __device__ __forceinline__ void fe_sqr_n(fe& r, const fe& a, int n) {
 // x30, x32, then 255 squarings and 12 multiplications in total.
 static __device__ __noinline__ void fe_inv(fe& r, const fe& a) {
     fe x2, x3, x6, x12, x15, x30, x32, t;
-    fe_sqr(t, a);       fe_mul(x2, t, a);      // 2^2 - 1
-    fe_sqr(t, x2);      fe_mul(x3, t, a);      // 2^3 - 1
-    fe_sqr_n(t, x3, 3); fe_mul(x6, t, x3);     // 2^6 - 1
-    fe_sqr_n(t, x6, 6); fe_mul(x12, t, x6);    // 2^12 - 1
-    fe_sqr_n(t, x12, 3); fe_mul(x15, t, x3);   // 2^15 - 1
-    fe_sqr_n(t, x15, 15); fe_mul(x30, t, x15); // 2^30 - 1
-    fe_sqr_n(t, x30, 2); fe_mul(x32, t, x2);   // 2^32 - 1
-    // bits 255..224: 32 ones
-    // bits 223..192: 0...01
-    fe_sqr_n(t, x32, 32); fe_mul(t, t, a);
+    x2 = fmul(fsqr(a), a);                       // 2^2 - 1
+    x3 = fmul(fsqr(x2), a);                      // 2^3 - 1
+    fe_sqr_n(t, x3, 3);  x6 = fmul(t, x3);       // 2^6 - 1
+    fe_sqr_n(t, x6, 6);  x12 = fmul(t, x6);      // 2^12 - 1
+    fe_sqr_n(t, x12, 3); x15 = fmul(t, x3);      // 2^15 - 1
+    fe_sqr_n(t, x15, 15); x30 = fmul(t, x15);    // 2^30 - 1
+    fe_sqr_n(t, x30, 2); x32 = fmul(t, x2);      // 2^32 - 1
+    // bits 255..224: 32 ones; bits 223..192: 0...01
+    fe_sqr_n(t, x32, 32); t = fmul(t, a);
     // bits 191..96: zeros
     fe_sqr_n(t, t, 96);
     // bits 95..32: 64 ones
-    fe_sqr_n(t, t, 32); fe_mul(t, t, x32);
-    fe_sqr_n(t, t, 32); fe_mul(t, t, x32);
+    fe_sqr_n(t, t, 32); t = fmul(t, x32);
+    fe_sqr_n(t, t, 32); t = fmul(t, x32);
     // bits 31..0: 30 ones, then 0, 1
-    fe_sqr_n(t, t, 30); fe_mul(t, t, x30);
-    fe_sqr_n(t, t, 2);  fe_mul(r, t, a);
+    fe_sqr_n(t, t, 30); t = fmul(t, x30);
+    fe_sqr_n(t, t, 2);  r = fmul(t, a);
+}
+
+// r = a b - c d (mod p) with a single reduction: the two 512-bit products
+// are subtracted, p 2^256 (= 0 mod p) is added back while the difference is
+// negative (once, or on a rare branch twice), then the sum is reduced.
+static __device__ __noinline__ fe fmulsub(fe a, fe b, fe c, fe d) {
+    uint32_t u[16], v[16];
+    mul_wide(u, a, b);
+    mul_wide(v, c, d);
+    uint32_t bw;
+    asm("sub.cc.u32  %0, %0, %17;\n\t"
+        "subc.cc.u32 %1, %1, %18;\n\t"
+        "subc.cc.u32 %2, %2, %19;\n\t"
+        "subc.cc.u32 %3, %3, %20;\n\t"
+        "subc.cc.u32 %4, %4, %21;\n\t"
+        "subc.cc.u32 %5, %5, %22;\n\t"
+        "subc.cc.u32 %6, %6, %23;\n\t"
+        "subc.cc.u32 %7, %7, %24;\n\t"
+        "subc.cc.u32 %8, %8, %25;\n\t"
+        "subc.cc.u32 %9, %9, %26;\n\t"
+        "subc.cc.u32 %10, %10, %27;\n\t"
+        "subc.cc.u32 %11, %11, %28;\n\t"
+        "subc.cc.u32 %12, %12, %29;\n\t"
+        "subc.cc.u32 %13, %13, %30;\n\t"
+        "subc.cc.u32 %14, %14, %31;\n\t"
+        "subc.cc.u32 %15, %15, %32;\n\t"
+        "subc.u32    %16, 0, 0;"
+        : "+r"(u[0]), "+r"(u[1]), "+r"(u[2]), "+r"(u[3]), "+r"(u[4]), "+r"(u[5]), "+r"(u[6]), "+r"(u[7]),
+          "+r"(u[8]), "+r"(u[9]), "+r"(u[10]), "+r"(u[11]), "+r"(u[12]), "+r"(u[13]), "+r"(u[14]),
+          "+r"(u[15]), "=r"(bw)
+        : "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+          "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]));
+    // On a borrow (bw = 0xffffffff) add p to the high half.
+    uint32_t c2;
+    asm("add.cc.u32  %0, %0, %9;\n\t"
+        "addc.cc.u32 %1, %1, %9;\n\t"
+        "addc.cc.u32 %2, %2, %9;\n\t"
+        "addc.cc.u32 %3, %3, 0;\n\t"
+        "addc.cc.u32 %4, %4, 0;\n\t"
+        "addc.cc.u32 %5, %5, 0;\n\t"
+        "addc.cc.u32 %6, %6, %10;\n\t"
+        "addc.cc.u32 %7, %7, %9;\n\t"
+        "addc.u32    %8, 0, 0;"
+        : "+r"(u[8]), "+r"(u[9]), "+r"(u[10]), "+r"(u[11]), "+r"(u[12]), "+r"(u[13]), "+r"(u[14]),
+          "+r"(u[15]), "=r"(c2)
+        : "r"(bw), "r"(bw & 1u));
+    if (bw && !c2) {  // still negative (needs c d - a b > p 2^256): add p 2^256 again
+        asm("add.cc.u32  %0, %0, 0xffffffff;\n\t"
+            "addc.cc.u32 %1, %1, 0xffffffff;\n\t"
+            "addc.cc.u32 %2, %2, 0xffffffff;\n\t"
+            "addc.cc.u32 %3, %3, 0;\n\t"
+            "addc.cc.u32 %4, %4, 0;\n\t"
+            "addc.cc.u32 %5, %5, 0;\n\t"
+            "addc.cc.u32 %6, %6, 1;\n\t"
+            "addc.u32    %7, %7, 0xffffffff;"
+            : "+r"(u[8]), "+r"(u[9]), "+r"(u[10]), "+r"(u[11]), "+r"(u[12]), "+r"(u[13]), "+r"(u[14]),
+              "+r"(u[15]));
+    }
+    fe r;
+    fe_reduce(r, u);
+    return r;
 }
 
 }  // namespace pcmm

@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(128) table_kernel(TableArgs a, PlanPtrs P) {
         fe z;
         lp_load_z(z, ents, e, lane);
         if (fe_is_zero(z)) fe_one(z);
-        fe_mul(acc, acc, z);
+        acc = fmul(acc, z);
         lp_store_fe(pref, e, lane, acc);
     }
     fe inv;
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(128) table_kernel(TableArgs a, PlanPtrs P) {
         if (e > 0) {
             fe pr;
             lp_load_fe(pr, pref, e - 1, lane);
-            fe_mul(zinv, inv, pr);
+            zinv = fmul(inv, pr);
         } else {
             zinv = inv;
         }
@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(128) table_kernel(TableArgs a, PlanPtrs P) {
         fe z = Pe.Z;
         const bool is_inf = fe_is_zero(z);
         if (is_inf) fe_one(z);
-        fe_mul(inv, inv, z);
+        inv = fmul(inv, z);
         aff out;
         if (is_inf) {
             fe_zero(out.x);
