@@ -156,6 +156,26 @@ size_t pcmm_cussen_workspace_bytes(int m, int n, int l, int w, int k);
 pcmm_status pcmm_cussen(const uint8_t *A, int m, int n, int w, const uint32_t *ctB, int l,
                         uint32_t *ctC, int k, void *ws, size_t ws_bytes, pcmm_stream_t stream);
 
+/* Cussen PC-MM that allocates nothing, for callers that may not allocate
+ * device memory (for instance a plug-in that is only handed its input and
+ * output buffers by a framework owning the device memory pool, or a
+ * latency-critical loop that cannot afford an allocation's implicit
+ * synchronisation).  The paper has no counterpart of this entry point.
+ * Same arguments (minus the workspace) and same result as pcmm_cussen.  The
+ * scratch space is a fixed 32 MiB array reserved by the library in global
+ * memory; every GPU on which the library is loaded holds it until the
+ * process exits.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) with the device current; make that first
+ * call before any stream capture.  All calls on a device share the one
+ * array, which keeps the last call's contents: the status word is cleared at
+ * the start of every call and everything else is written before it is read,
+ * but calls that overlap on the GPU (for instance on two streams without an
+ * ordering between them) race on the array and corrupt each other's results.
+ * Errors: PCMM_EUNSUPPORTED when the problem needs more than the 32 MiB
+ * (nothing is launched then), otherwise as pcmm_cussen. */
+pcmm_status pcmm_cussen_static(const uint8_t *A, int m, int n, int w, const uint32_t *ctB, int l,
+                               uint32_t *ctC, int k, pcmm_stream_t stream);
+
 /* Reads the status word of a pcmm_cussen workspace into *status_host after
  * synchronising `stream`.  0 means no kernel raised an error bit. */
 pcmm_status pcmm_workspace_status(const void *ws, uint32_t *status_host, pcmm_stream_t stream);
