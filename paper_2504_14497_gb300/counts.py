@@ -37,38 +37,53 @@ def _levels(col: np.ndarray, N: int = N_ITER):
 
 
 def cussen_counts(A: np.ndarray, w: int, k: int, l: int, N: int = N_ITER) -> dict:
+    """Operations of one Cussen PC-MM for the l useful output columns (both
+    ciphertext components), as the table and gather kernels perform them:
+
+    * ``table_dbl``/``table_ecsm_madd``: double-and-add of the level-N values;
+    * ``table_add``: prefix sums of levels N-1..2 (Jacobian + Jacobian);
+    * ``table_madd``: level-1 prefix sums and k-tuple sums (Jacobian + affine);
+    * ``table_norm``: entries normalised to affine (level 2, column tables when
+      k > 1, strip tables);
+    * ``gather_madd``: accumulations of table entries into the outputs.
+    Additions with an identity operand are copies and are not counted."""
     A = np.asarray(A).astype(np.int64) & ((1 << w) - 1)
     m, n = A.shape
     chains = 2 * l
-    gather = 0
-    tadd = tmadd = tdbl = norm = 0
+    tadd = tmadd = tdbl = tecsm = norm = 0
     nnz_rows = np.zeros(m, dtype=np.int64)
     for s0 in range(0, n, k):
         cols = A[:, s0:s0 + k]
+        kw = cols.shape[1]
         codes = np.zeros(m, dtype=np.int64)
-        for t in range(cols.shape[1]):
+        for t in range(kw):
             codes |= cols[:, t] << (w * t)
             lens, vN = _levels(cols[:, t], N)
             for v in vN:
                 v = int(v)
                 tdbl += chains * (v.bit_length() - 1)
-                tmadd += chains * (bin(v).count("1") - 1)
-            tadd += chains * sum(max(x - 1, 0) for x in lens[:-1])
+                tecsm += chains * (bin(v).count("1") - 1)
+            tadd += chains * sum(max(x - 1, 0) for x in lens[1:-1])
+            tmadd += chains * max(lens[0] - 1, 0)
+            norm += chains * (lens[1] if N > 1 else 0)
+            if kw > 1:
+                norm += chains * lens[0]
         distinct = np.unique(codes[codes != 0])
-        if cols.shape[1] > 1:
+        if kw > 1:
             for code in distinct:
-                parts = sum(1 for t in range(cols.shape[1]) if (int(code) >> (w * t)) & ((1 << w) - 1))
-                tadd += chains * max(parts - 1, 0)
+                parts = sum(1 for t in range(kw) if (int(code) >> (w * t)) & ((1 << w) - 1))
+                tmadd += chains * max(parts - 1, 0)
         norm += chains * len(distinct)
         nnz_rows += codes != 0
     gather = chains * int(np.maximum(nnz_rows - 1, 0).sum())
     return {"gather_madd": gather, "table_add": tadd, "table_madd": tmadd, "table_dbl": tdbl,
-            "table_norm": norm}
+            "table_ecsm_madd": tecsm, "table_norm": norm}
 
 
 def point_ops(c: dict) -> int:
     """Point additions and doublings of two finite points performed."""
-    return c["gather_madd"] + c["table_add"] + c["table_madd"] + c["table_dbl"]
+    return (c["gather_madd"] + c["table_add"] + c["table_madd"] + c["table_dbl"]
+            + c["table_ecsm_madd"])
 
 
 def gather_imad(c: dict) -> int:
@@ -76,7 +91,8 @@ def gather_imad(c: dict) -> int:
 
 
 def table_imad(c: dict) -> int:
-    p = (c["table_add"] * PRODUCTS["add"] + c["table_madd"] * PRODUCTS["madd"]
+    p = (c["table_add"] * PRODUCTS["add"]
+         + (c["table_madd"] + c["table_ecsm_madd"]) * PRODUCTS["madd"]
          + c["table_dbl"] * PRODUCTS["dbl"] + c["table_norm"] * PRODUCTS["norm"])
     return p * IMAD_PER_PRODUCT
 

@@ -80,8 +80,12 @@ bool make_layout(Layout& L, int m, int n, int l, int w, int k) {
     L.off_ptr = off;   off = align256(off + (size_t)n * (NLEV > 1 ? NLEV - 1 : 1) * 256);
     L.off_rank1 = off; off = align256(off + (size_t)n * 256);
     L.plan_bytes = off;
-    const size_t ent_jac = (size_t)k * L.n1max + 2 * (size_t)L.l2max + (k > 1 ? (size_t)L.emax : 0);
-    L.item_u4 = ent_jac * 6 * 32 + (size_t)L.emax * 2 * 32;
+    // Per warp item (lane-planar): Jacobian column table and level ping-pong,
+    // affine level-2 entries, affine column tables and Jacobian tuples (k > 1),
+    // prefix products for the normalisations.
+    const size_t jac_ents = (size_t)L.n1max + 2 * (size_t)L.l2max + (k > 1 ? (size_t)L.emax : 0);
+    const size_t aff_ents = (size_t)L.l2max + (k > 1 ? (size_t)k * L.n1max : 0);
+    L.item_u4 = jac_ents * 6 * 32 + aff_ents * 4 * 32 + (size_t)L.emax * 2 * 32;
     L.items_per_strip = 2 * (size_t)L.njb;
     L.table_points_per_strip = (size_t)L.emax * 2 * L.lp;
     L.per_strip_bytes = L.items_per_strip * L.item_u4 * 16 + align256(L.table_points_per_strip * 64);
@@ -260,7 +264,88 @@ struct TableArgs {
     size_t table_points;
 };
 
+__device__ __forceinline__ void lp_store_aff(uint4* base, int e, unsigned lane, const aff& Q) {
+    uint4* b = base + (size_t)e * 4 * 32 + lane;
+    b[0] = fe_lo(Q.x);
+    b[32] = fe_hi(Q.x);
+    b[64] = fe_lo(Q.y);
+    b[96] = fe_hi(Q.y);
+}
+
+__device__ __forceinline__ void lp_load_aff(aff& Q, const uint4* base, int e, unsigned lane) {
+    const uint4* b = base + (size_t)e * 4 * 32 + lane;
+    fe_from_quads(Q.x, b[0], b[32]);
+    fe_from_quads(Q.y, b[64], b[96]);
+}
+
+__device__ __forceinline__ bool fe_is_one(const fe& a) {
+    uint32_t z = (a.v[0] ^ 1u) | a.v[1] | a.v[2] | a.v[3] | a.v[4] | a.v[5] | a.v[6] | a.v[7];
+    return z == 0u;
+}
+
+// Normalises E lane-planar Jacobian entries to canonical affine (infinity ->
+// (0, 0)) and hands entry e to store(e, point).  Montgomery's simultaneous
+// inversion: per-lane prefix products of the Z's (kept in pref), then one
+// warp-wide inversion.  When every Z in the warp is already 1 the entries
+// are copied without any inversion.  All 32 lanes call with the same E.
+template <class Store>
+__device__ __forceinline__ void lp_normalize(const uint4* src, int E, uint4* pref, unsigned lane,
+                                             Store store) {
+    if (E <= 0) return;
+    bool ones = true;
+    fe acc;
+    fe_one(acc);
+    for (int e = 0; e < E; e++) {
+        fe z;
+        lp_load_z(z, src, e, lane);
+        ones &= fe_is_one(z);
+        if (fe_is_zero(z)) fe_one(z);
+        acc = fmul(acc, z);
+        lp_store_fe(pref, e, lane, acc);
+    }
+    if (__all_sync(0xffffffffu, ones)) {
+        for (int e = 0; e < E; e++) {
+            jac Pe;
+            lp_load_jac(Pe, src, e, lane);
+            aff out;
+            fe_canon(out.x, Pe.X);
+            fe_canon(out.y, Pe.Y);
+            store(e, out);
+        }
+        return;
+    }
+    fe inv;
+    warp_inverse(inv, acc);
+    for (int e = E - 1; e >= 0; e--) {
+        fe zinv;
+        if (e > 0) {
+            fe pr;
+            lp_load_fe(pr, pref, e - 1, lane);
+            zinv = fmul(inv, pr);
+        } else {
+            zinv = inv;
+        }
+        jac Pe;
+        lp_load_jac(Pe, src, e, lane);
+        fe z = Pe.Z;
+        const bool is_inf = fe_is_zero(z);
+        if (is_inf) fe_one(z);
+        inv = fmul(inv, z);
+        aff out;
+        if (is_inf) {
+            fe_zero(out.x);
+            fe_zero(out.y);
+        } else {
+            jac_to_aff_with_zinv(out, Pe, zinv);
+        }
+        store(e, out);
+    }
+}
+
+// One warp per (strip, component c, 32 output columns); all lanes follow the
+// same plan, so the control flow is warp-uniform.
 __global__ void __launch_bounds__(128) table_kernel(TableArgs a, PlanPtrs P) {
+    static_assert(NLEV >= 2, "the table build assumes at least two compression levels");
     const unsigned lane = threadIdx.x & 31u;
     const long long item = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nitems = (long long)a.nstrips_chunk * 2 * a.njb;
@@ -277,19 +362,24 @@ __global__ void __launch_bounds__(128) table_kernel(TableArgs a, PlanPtrs P) {
     const uint4* Bc = a.ctB + (size_t)c * 4 * nl;
     const uint32_t amask = (1u << a.w) - 1u;
 
-    uint4* base = a.scratch + (size_t)item * a.item_u4;
-    uint4* coltab = base;
-    uint4* levA = coltab + (size_t)a.k * a.n1max * 192;
-    uint4* levB = levA + (size_t)a.l2max * 192;
-    uint4* ents_x = levB + (size_t)a.l2max * 192;
-    uint4* pref = ents_x + (a.k > 1 ? (size_t)a.emax * 192 : 0);
+    // Scratch regions of this warp item (see make_layout).
+    uint4* coltab = a.scratch + (size_t)item * a.item_u4;                 // n1max Jacobian
+    uint4* levA = coltab + (size_t)a.n1max * 192;                         // l2max Jacobian
+    uint4* levB = levA + (size_t)a.l2max * 192;                           // l2max Jacobian
+    uint4* ents_x = levB + (size_t)a.l2max * 192;                         // emax Jacobian (k > 1)
+    uint4* l2aff = ents_x + (a.k > 1 ? (size_t)a.emax * 192 : 0);         // l2max affine
+    uint4* colaff = l2aff + (size_t)a.l2max * 128;                        // k * n1max affine (k > 1)
+    uint4* pref = colaff + (a.k > 1 ? (size_t)a.k * a.n1max * 128 : 0);   // emax field elements
 
     const int E = P.nent[s];
+    const size_t tbase = (size_t)s_local * a.emax;
+    auto store_table = [&](int e, const aff& q) {
+        store_aff(a.table, a.table_points, ((tbase + e) * 2 + c) * a.lp + j, q);
+    };
     bool bad = false;
 
     for (int t = 0; t < kw; t++) {
         const int col = c0 + t;
-        uint4* ct_t = coltab + (size_t)t * a.n1max * 192;
         aff Pb;
         load_aff(Pb, Bc, nl, (size_t)col * a.l + jj);
         int lens[NLEV];
@@ -300,91 +390,69 @@ __global__ void __launch_bounds__(128) table_kernel(TableArgs a, PlanPtrs P) {
         for (int q = 1; q < NLEV; q++) bad |= lens[q] > a.l2max;
         if (bad) break;
         // Level N: multiples of the compressed values (double-and-add).
-        uint4* src = (NLEV == 1) ? ct_t : levA;
+        uint4* src = levA;
         for (int e = 0; e < lens[NLEV - 1]; e++) {
             jac T;
             jac_mul_small(T, Pb, P.col_vN[(size_t)col * 256 + e]);
             lp_store_jac(src, e, lane, T);
         }
         uint4* alt = levB;
-        // Levels N-1..1: un-sort by the tracking pointers, then prefix sums.
-        for (int lev = NLEV - 1; lev >= 1; lev--) {
-            uint4* dst = (lev == 1) ? ct_t : alt;
+        // Levels N-1..2: un-sort by the tracking pointers, then prefix sums.
+        for (int lev = NLEV - 1; lev >= 2; lev--) {
             const uint8_t* ptr = P.col_ptr + ((size_t)col * (NLEV - 1) + (lev - 1)) * 256;
             jac acc, D;
             jac_set_inf(acc);
             for (int e = 0; e < lens[lev - 1]; e++) {
                 lp_load_jac(D, src, ptr[e], lane);
                 jac_add(acc, D);
-                lp_store_jac(dst, e, lane, acc);
+                lp_store_jac(alt, e, lane, acc);
             }
-            alt = src;
-            src = dst;
+            uint4* tmp = src; src = alt; alt = tmp;
         }
+        // Level 2 (multiples of the level-1 differences) to affine, so that
+        // the level-1 prefix sums are mixed additions.
+        lp_normalize(src, lens[1], pref, lane, [&](int e, const aff& q) { lp_store_aff(l2aff, e, lane, q); });
+        // Level 1: the multiples of the column's sorted distinct values.
+        {
+            const uint8_t* ptr = P.col_ptr + (size_t)col * (NLEV - 1) * 256;
+            jac acc;
+            aff D;
+            jac_set_inf(acc);
+            for (int e = 0; e < lens[0]; e++) {
+                lp_load_aff(D, l2aff, ptr[e], lane);
+                jac_madd(acc, D);
+                lp_store_jac(coltab, e, lane, acc);
+            }
+        }
+        if (a.k == 1) {
+            // The column table is the strip table.
+            lp_normalize(coltab, E, pref, lane, store_table);
+            return;
+        }
+        uint4* ca = colaff + (size_t)t * a.n1max * 128;
+        lp_normalize(coltab, lens[0], pref, lane, [&](int e, const aff& q) { lp_store_aff(ca, e, lane, q); });
     }
     if (bad) {
         if (lane == 0) atomicOr(P.status, DEV_ERR_PLAN);
         return;
     }
-
-    // Entries of the strip table (Jacobian).
-    uint4* ents = coltab;
-    if (a.k > 1) {
-        ents = ents_x;
-        for (int e = 0; e < E; e++) {
-            const uint32_t code = P.codes[(size_t)s * a.emax + e];
-            jac acc, D;
-            jac_set_inf(acc);
-            for (int t = 0; t < kw; t++) {
-                const uint32_t v = (code >> (a.w * t)) & amask;
-                if (v) {
-                    const int r1 = P.col_rank1[(size_t)(c0 + t) * 256 + v];
-                    lp_load_jac(D, coltab + (size_t)t * a.n1max * 192, r1, lane);
-                    jac_add(acc, D);
-                }
-            }
-            lp_store_jac(ents, e, lane, acc);
-        }
-    }
-    if (E == 0) return;
-
-    // Affine normalisation of the E entries (simultaneous inversion).
-    fe acc;
-    fe_one(acc);
+    // k > 1: one entry per distinct k-tuple, the sum of its columns' entries.
     for (int e = 0; e < E; e++) {
-        fe z;
-        lp_load_z(z, ents, e, lane);
-        if (fe_is_zero(z)) fe_one(z);
-        acc = fmul(acc, z);
-        lp_store_fe(pref, e, lane, acc);
-    }
-    fe inv;
-    warp_inverse(inv, acc);
-    const size_t tbase = (size_t)s_local * a.emax;
-    for (int e = E - 1; e >= 0; e--) {
-        fe zinv;
-        if (e > 0) {
-            fe pr;
-            lp_load_fe(pr, pref, e - 1, lane);
-            zinv = fmul(inv, pr);
-        } else {
-            zinv = inv;
+        const uint32_t code = P.codes[(size_t)s * a.emax + e];
+        jac acc;
+        aff D;
+        jac_set_inf(acc);
+        for (int t = 0; t < kw; t++) {
+            const uint32_t v = (code >> (a.w * t)) & amask;
+            if (v) {
+                const int r1 = P.col_rank1[(size_t)(c0 + t) * 256 + v];
+                lp_load_aff(D, colaff + (size_t)t * a.n1max * 128, r1, lane);
+                jac_madd(acc, D);
+            }
         }
-        jac Pe;
-        lp_load_jac(Pe, ents, e, lane);
-        fe z = Pe.Z;
-        const bool is_inf = fe_is_zero(z);
-        if (is_inf) fe_one(z);
-        inv = fmul(inv, z);
-        aff out;
-        if (is_inf) {
-            fe_zero(out.x);
-            fe_zero(out.y);
-        } else {
-            jac_to_aff_with_zinv(out, Pe, zinv);
-        }
-        store_aff(a.table, a.table_points, ((tbase + e) * 2 + c) * a.lp + j, out);
+        lp_store_jac(ents_x, e, lane, acc);
     }
+    lp_normalize(ents_x, E, pref, lane, store_table);
 }
 
 struct GatherArgs {
