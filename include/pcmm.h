@@ -156,6 +156,28 @@ size_t pcmm_cussen_workspace_bytes(int m, int n, int l, int w, int k);
 pcmm_status pcmm_cussen(const uint8_t *A, int m, int n, int w, const uint32_t *ctB, int l,
                         uint32_t *ctC, int k, void *ws, size_t ws_bytes, pcmm_stream_t stream);
 
+/* The same computation in two phases, so that the plan of a plaintext matrix
+ * (it depends on A, w and k only: Algorithm 3 compresses each column of A
+ * once for all columns of Enc(B)) can stay resident and serve many Enc(B).
+ * pcmm_cussen_plan_bytes: bytes of the plan of an m x n matrix (k >= 1
+ *   required), 0 for invalid arguments.
+ * pcmm_cussen_plan: builds the plan of A into `plan` (device, 256-byte
+ *   aligned, >= pcmm_cussen_plan_bytes), clearing its status word (first 4
+ *   bytes; read it with pcmm_workspace_status).
+ * pcmm_cussen_exec_bytes: scratch bytes for one execution with l columns
+ *   (a default number of strips per pass; any multiple of one strip's need
+ *   works, larger means fewer passes).
+ * pcmm_cussen_execute: ctC = A Enc(B) using a plan built with the same m, n,
+ *   w, k (not checked).  The plan is only read, so executions with their own
+ *   scratch `ws` may run concurrently on different streams.
+ * Errors: PCMM_EINVAL, PCMM_ENOMEM (plan or scratch too small), PCMM_ECUDA. */
+size_t pcmm_cussen_plan_bytes(int m, int n, int w, int k);
+pcmm_status pcmm_cussen_plan(const uint8_t *A, int m, int n, int w, int k, void *plan,
+                             size_t plan_bytes, pcmm_stream_t stream);
+size_t pcmm_cussen_exec_bytes(int m, int n, int l, int w, int k);
+pcmm_status pcmm_cussen_execute(const void *plan, int m, int n, int w, int k, const uint32_t *ctB,
+                                int l, uint32_t *ctC, void *ws, size_t ws_bytes, pcmm_stream_t stream);
+
 /* Cussen PC-MM that allocates nothing, for callers that may not allocate
  * device memory (for instance a plug-in that is only handed its input and
  * output buffers by a framework owning the device memory pool, or a
@@ -186,6 +208,17 @@ pcmm_status pcmm_workspace_status(const void *ws, uint32_t *status_host, pcmm_st
  * (may not overlap).  Errors: PCMM_EINVAL, PCMM_ECUDA. */
 pcmm_status pcmm_normalize(const uint32_t *ct_jac, size_t count, uint32_t *ct_aff,
                            pcmm_stream_t stream);
+
+/* Copies a block of 16-byte words between two row-major matrices of 16-byte
+ * words: dst[r * dst_ld + dst_col + c] = src[r * src_ld + src_col + c] for
+ * r < nrows, c < ncols (one asynchronous 2-D copy on `stream`).  A quad-planar
+ * ciphertext matrix with R rows and L columns is such a matrix with
+ * 8 R rows (affine; 12 R if Jacobian) and leading dimension L, so this packs
+ * the columns of several Enc(B) into one batch and splits a batched result
+ * back.  Errors: PCMM_EINVAL (null pointers, columns out of range), PCMM_ECUDA. */
+pcmm_status pcmm_copy_columns(uint32_t *dst, size_t dst_ld, size_t dst_col, const uint32_t *src,
+                              size_t src_ld, size_t src_col, size_t ncols, size_t nrows,
+                              pcmm_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * Per-kernel timing.  pcmm_profile_enable(capacity > 0) creates `capacity`

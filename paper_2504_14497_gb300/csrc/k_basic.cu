@@ -295,6 +295,20 @@ extern "C" pcmm_status pcmm_normalize(const uint32_t* ct_jac, size_t count, uint
     return PCMM_OK;
 }
 
+extern "C" pcmm_status pcmm_copy_columns(uint32_t* dst, size_t dst_ld, size_t dst_col,
+                                         const uint32_t* src, size_t src_ld, size_t src_col,
+                                         size_t ncols, size_t nrows, pcmm_stream_t stream) {
+    if (!dst || !src || ncols > dst_ld || ncols > src_ld || dst_col + ncols > dst_ld ||
+        src_col + ncols > src_ld)
+        return PCMM_EINVAL;
+    if (ncols == 0 || nrows == 0) return PCMM_OK;
+    if (cudaMemcpy2DAsync((uint8_t*)dst + dst_col * 16, dst_ld * 16, (const uint8_t*)src + src_col * 16,
+                          src_ld * 16, ncols * 16, nrows, cudaMemcpyDefault,
+                          (cudaStream_t)stream) != cudaSuccess)
+        return PCMM_ECUDA;
+    return PCMM_OK;
+}
+
 extern "C" pcmm_status pcmm_test_field(int op, const uint32_t* a, const uint32_t* b, uint32_t* out,
                                        size_t count, pcmm_stream_t stream) {
     if (op < 0 || op > 5 || !a || !out || (op <= 2 && !b)) return PCMM_EINVAL;

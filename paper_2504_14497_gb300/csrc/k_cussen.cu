@@ -539,34 +539,34 @@ extern "C" size_t pcmm_cussen_workspace_bytes(int m, int n, int l, int w, int k)
     return L.plan_bytes + S * L.per_strip_bytes;
 }
 
-extern "C" pcmm_status pcmm_cussen(const uint8_t* A, int m, int n, int w, const uint32_t* ctB, int l,
-                                   uint32_t* ctC, int k, void* ws, size_t ws_bytes,
-                                   pcmm_stream_t stream) {
-    if (!A || !ctB || !ctC || !ws || ((uintptr_t)ws & 255u)) return PCMM_EINVAL;
-    if (m < 1 || n < 1 || l < 1 || w < 1 || w > PCMM_MAX_W) return PCMM_EINVAL;
-    if (k == 0) k = pcmm_cussen_choose_k(m, n, l, w);
-    Layout L;
-    if (!make_layout(L, m, n, l, w, k)) return PCMM_EINVAL;
-    if (ws_bytes < L.plan_bytes + L.per_strip_bytes) return PCMM_ENOMEM;
-    size_t S = (ws_bytes - L.plan_bytes) / L.per_strip_bytes;
-    if (S > (size_t)L.nstrips) S = L.nstrips;
-    cudaStream_t st = (cudaStream_t)stream;
-    PlanPtrs P = plan_ptrs(L, ws);
-    uint8_t* chunk = (uint8_t*)ws + L.plan_bytes;
-    uint4* scratch = (uint4*)chunk;
-    uint4* table = (uint4*)(chunk + align256(S * L.items_per_strip * L.item_u4 * 16));
+namespace {
+size_t default_strips(const Layout& L);
+}
+
+namespace {
+
+pcmm_status launch_plan(const Layout& L, const uint8_t* A, const PlanPtrs& P, cudaStream_t st) {
     if (cudaMemsetAsync(P.status, 0, 4, st) != cudaSuccess) return PCMM_ECUDA;
     {
         ProfScope ps(KID_PLAN, st);
-        plan_kernel<<<L.nstrips, PLAN_THREADS, 0, st>>>(A, m, n, w, k, L.emax, P);
+        plan_kernel<<<L.nstrips, PLAN_THREADS, 0, st>>>(A, L.m, L.n, L.w, L.k, L.emax, P);
     }
     PCMM_CUDA_CHECK_LAUNCH();
+    return PCMM_OK;
+}
+
+// Table build and gather over chunks of S strips, using the scratch area at
+// `chunk` (S * per_strip_bytes bytes).
+pcmm_status launch_exec(const Layout& L, const PlanPtrs& P, const uint32_t* ctB, uint32_t* ctC,
+                        uint8_t* chunk, size_t S, cudaStream_t st) {
+    uint4* scratch = (uint4*)chunk;
+    uint4* table = (uint4*)(chunk + align256(S * L.items_per_strip * L.item_u4 * 16));
     for (int s0 = 0; s0 < L.nstrips; s0 += (int)S) {
         const int sc = (int)((size_t)(L.nstrips - s0) < S ? (size_t)(L.nstrips - s0) : S);
         TableArgs ta;
         ta.ctB = (const uint4*)ctB;
-        ta.A = A;
-        ta.m = m; ta.n = n; ta.l = l; ta.w = w; ta.k = k;
+        ta.A = nullptr;
+        ta.m = L.m; ta.n = L.n; ta.l = L.l; ta.w = L.w; ta.k = L.k;
         ta.lp = L.lp; ta.njb = L.njb; ta.n1max = L.n1max; ta.l2max = L.l2max; ta.emax = L.emax;
         ta.s0 = s0; ta.nstrips_chunk = sc;
         ta.scratch = scratch;
@@ -580,13 +580,13 @@ extern "C" pcmm_status pcmm_cussen(const uint8_t* A, int m, int n, int w, const 
         }
         PCMM_CUDA_CHECK_LAUNCH();
         GatherArgs ga;
-        ga.m = m; ga.l = l; ga.lp = L.lp; ga.njb = L.njb; ga.emax = L.emax;
+        ga.m = L.m; ga.l = L.l; ga.lp = L.lp; ga.njb = L.njb; ga.emax = L.emax;
         ga.s0 = s0; ga.nstrips_chunk = sc;
         ga.first = (s0 == 0);
         ga.table = table;
         ga.table_points = ta.table_points;
         ga.ctC = (uint4*)ctC;
-        const long long warps = (long long)m * 2 * L.njb;
+        const long long warps = (long long)L.m * 2 * L.njb;
         {
             ProfScope ps(KID_GATHER, st);
             gather_kernel<<<(unsigned)((warps + 3) / 4), 128, 0, st>>>(ga, P);
@@ -594,6 +594,67 @@ extern "C" pcmm_status pcmm_cussen(const uint8_t* A, int m, int n, int w, const 
         PCMM_CUDA_CHECK_LAUNCH();
     }
     return PCMM_OK;
+}
+
+size_t default_strips(const Layout& L) {
+    size_t S = (TARGET_ITEMS + L.items_per_strip - 1) / L.items_per_strip;
+    if (S > (size_t)L.nstrips) S = L.nstrips;
+    return S < 1 ? 1 : S;
+}
+
+}  // namespace
+
+extern "C" pcmm_status pcmm_cussen(const uint8_t* A, int m, int n, int w, const uint32_t* ctB, int l,
+                                   uint32_t* ctC, int k, void* ws, size_t ws_bytes,
+                                   pcmm_stream_t stream) {
+    if (!A || !ctB || !ctC || !ws || ((uintptr_t)ws & 255u)) return PCMM_EINVAL;
+    if (m < 1 || n < 1 || l < 1 || w < 1 || w > PCMM_MAX_W) return PCMM_EINVAL;
+    if (k == 0) k = pcmm_cussen_choose_k(m, n, l, w);
+    Layout L;
+    if (!make_layout(L, m, n, l, w, k)) return PCMM_EINVAL;
+    if (ws_bytes < L.plan_bytes + L.per_strip_bytes) return PCMM_ENOMEM;
+    size_t S = (ws_bytes - L.plan_bytes) / L.per_strip_bytes;
+    if (S > (size_t)L.nstrips) S = L.nstrips;
+    cudaStream_t st = (cudaStream_t)stream;
+    PlanPtrs P = plan_ptrs(L, ws);
+    pcmm_status rc = launch_plan(L, A, P, st);
+    if (rc != PCMM_OK) return rc;
+    return launch_exec(L, P, ctB, ctC, (uint8_t*)ws + L.plan_bytes, S, st);
+}
+
+extern "C" size_t pcmm_cussen_plan_bytes(int m, int n, int w, int k) {
+    Layout L;
+    if (!make_layout(L, m, n, 1, w, k)) return 0;
+    return L.plan_bytes;
+}
+
+extern "C" pcmm_status pcmm_cussen_plan(const uint8_t* A, int m, int n, int w, int k, void* plan,
+                                        size_t plan_bytes, pcmm_stream_t stream) {
+    if (!A || !plan || ((uintptr_t)plan & 255u)) return PCMM_EINVAL;
+    Layout L;
+    if (!make_layout(L, m, n, 1, w, k)) return PCMM_EINVAL;
+    if (plan_bytes < L.plan_bytes) return PCMM_ENOMEM;
+    return launch_plan(L, A, plan_ptrs(L, plan), (cudaStream_t)stream);
+}
+
+extern "C" size_t pcmm_cussen_exec_bytes(int m, int n, int l, int w, int k) {
+    Layout L;
+    if (!make_layout(L, m, n, l, w, k)) return 0;
+    return default_strips(L) * L.per_strip_bytes;
+}
+
+extern "C" pcmm_status pcmm_cussen_execute(const void* plan, int m, int n, int w, int k,
+                                           const uint32_t* ctB, int l, uint32_t* ctC, void* ws,
+                                           size_t ws_bytes, pcmm_stream_t stream) {
+    if (!plan || !ctB || !ctC || !ws || ((uintptr_t)plan & 255u) || ((uintptr_t)ws & 255u))
+        return PCMM_EINVAL;
+    Layout L;
+    if (!make_layout(L, m, n, l, w, k)) return PCMM_EINVAL;
+    if (ws_bytes < L.per_strip_bytes) return PCMM_ENOMEM;
+    size_t S = ws_bytes / L.per_strip_bytes;
+    if (S > (size_t)L.nstrips) S = L.nstrips;
+    return launch_exec(L, plan_ptrs(L, const_cast<void*>(plan)), ctB, ctC, (uint8_t*)ws, S,
+                       (cudaStream_t)stream);
 }
 
 extern "C" pcmm_status pcmm_workspace_status(const void* ws, uint32_t* status_host, pcmm_stream_t stream) {

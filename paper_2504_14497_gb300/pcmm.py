@@ -26,7 +26,8 @@ PCMM_JAC_WORDS = 48
 EXPORTS = (
     "pcmm_version", "pcmm_status_string", "pcmm_init", "pcmm_keytable_bytes", "pcmm_keytable",
     "pcmm_encrypt", "pcmm_base_mul", "pcmm_schoolbook", "pcmm_cussen_choose_k", "pcmm_cussen_workspace_bytes",
-    "pcmm_cussen", "pcmm_workspace_status", "pcmm_normalize", "pcmm_profile_enable",
+    "pcmm_cussen", "pcmm_cussen_plan_bytes", "pcmm_cussen_plan", "pcmm_cussen_exec_bytes",
+    "pcmm_cussen_execute", "pcmm_workspace_status", "pcmm_copy_columns", "pcmm_normalize", "pcmm_profile_enable",
     "pcmm_profile_read", "pcmm_kernel_count", "pcmm_kernel_name", "pcmm_test_field", "pcmm_test_point",
 )
 
@@ -62,7 +63,12 @@ def lib():
                 "pcmm_cussen_choose_k": ([ci, ci, ci, ci], ci),
                 "pcmm_cussen_workspace_bytes": ([ci, ci, ci, ci, ci], sz),
                 "pcmm_cussen": ([vp, ci, ci, ci, vp, ci, vp, ci, vp, sz, vp], ci),
+                "pcmm_cussen_plan_bytes": ([ci, ci, ci, ci], sz),
+                "pcmm_cussen_plan": ([vp, ci, ci, ci, ci, vp, sz, vp], ci),
+                "pcmm_cussen_exec_bytes": ([ci, ci, ci, ci, ci], sz),
+                "pcmm_cussen_execute": ([vp, ci, ci, ci, ci, vp, ci, vp, vp, sz, vp], ci),
                 "pcmm_workspace_status": ([vp, u32p, vp], ci),
+                "pcmm_copy_columns": ([vp, sz, sz, vp, sz, sz, sz, sz, vp], ci),
                 "pcmm_normalize": ([vp, sz, vp, vp], ci),
                 "pcmm_test_field": ([ci, vp, vp, vp, sz, vp], ci),
                 "pcmm_test_point": ([ci, vp, vp, vp, vp, sz, vp], ci),
@@ -253,6 +259,42 @@ def cussen(A, ctB, l: int, w: int, k: int = 0, ws=None, out=None, stream=None):
     _check(lib().pcmm_cussen(_ptr(A), m, n, w, _ptr(ctB), l, _ptr(out), k, _ptr(ws), ws.numel(),
                              _stream(stream)), "pcmm_cussen")
     return out
+
+
+class Plan:
+    """A resident Cussen plan of one plaintext matrix A (device memory)."""
+
+    def __init__(self, A, w: int, k: int, stream=None):
+        torch = _torch()
+        self.m, self.n = A.shape
+        self.w, self.k = int(w), int(k)
+        nb = int(lib().pcmm_cussen_plan_bytes(self.m, self.n, self.w, self.k))
+        if nb == 0:
+            raise ValueError("invalid plan shape")
+        self.buf = torch.empty(nb, dtype=torch.uint8, device=A.device)
+        _check(lib().pcmm_cussen_plan(_ptr(A), self.m, self.n, self.w, self.k, _ptr(self.buf), nb,
+                                      _stream(stream)), "pcmm_cussen_plan")
+
+    def exec_bytes(self, l: int) -> int:
+        return int(lib().pcmm_cussen_exec_bytes(self.m, self.n, l, self.w, self.k))
+
+    def execute(self, ctB, l: int, ws=None, out=None, stream=None):
+        torch = _torch()
+        if ws is None:
+            ws = torch.empty(self.exec_bytes(l), dtype=torch.uint8, device=ctB.device)
+        if out is None:
+            out = torch.empty(PCMM_JAC_WORDS * self.m * l, dtype=torch.int32, device=ctB.device)
+        _check(lib().pcmm_cussen_execute(_ptr(self.buf), self.m, self.n, self.w, self.k, _ptr(ctB), l,
+                                         _ptr(out), _ptr(ws), ws.numel(), _stream(stream)),
+               "pcmm_cussen_execute")
+        return out
+
+
+def copy_columns(dst, dst_ld: int, dst_col: int, src, src_ld: int, src_col: int, ncols: int,
+                 nrows: int, stream=None):
+    """Block copy of ncols 16-byte columns over nrows rows (see pcmm.h)."""
+    _check(lib().pcmm_copy_columns(_ptr(dst), dst_ld, dst_col, _ptr(src), src_ld, src_col, ncols, nrows,
+                                   _stream(stream)), "pcmm_copy_columns")
 
 
 def workspace_status(ws, stream=None) -> int:

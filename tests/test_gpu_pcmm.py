@@ -228,3 +228,52 @@ def test_base_mul_keygen_matches_oracle(dev):
     want = oracle.base_mul(sk)
     assert (got == want).all()
     assert (pcmm.public_key(sk[5], device=dev) == oracle.keygen(sk[5])).all()
+
+
+def test_resident_plan_serves_several_inputs(dev):
+    # Plan once (it depends on A only), execute for two Enc(B) of different widths.
+    m, n, w, k = 50, 33, 4, 2
+    plan = None
+    for l, seed in ((7, 1001), (40, 1002)):
+        pr = inputs.pcmm_problem(seed, m, n, l, w)
+        if plan is None:
+            A_host = pr["A"]
+            plan = pcmm.Plan(torch.from_numpy(A_host).to(dev), w, k)
+        pr["A"] = A_host
+        ctB = encrypt_gpu(dev, pr)
+        got = run_affine(lambda: plan.execute(ctB, l), m * l)
+        assert mismatches(got, _want(pr)) == 0
+        # Smaller scratch: more passes, same result.
+        ws = torch.empty(plan.exec_bytes(l) // 3 + 256, dtype=torch.uint8, device=dev)
+        try:
+            got2 = run_affine(lambda: plan.execute(ctB, l, ws=ws), m * l)
+            assert mismatches(got2, _want(pr)) == 0
+        except pcmm.PcmmError as e:
+            assert e.status == 2
+
+
+def test_copy_columns_packs_and_splits(dev):
+    m, n, w = 20, 12, 3
+    parts = []
+    for l, seed in ((3, 2001), (5, 2002), (1, 2003)):
+        pr = inputs.pcmm_problem(seed, m, n, l, w)
+        parts.append((pr, encrypt_gpu(dev, pr), l))
+    L = sum(p[2] for p in parts)
+    batch = torch.empty(32 * n * L, dtype=torch.int32, device=dev)
+    off = 0
+    for pr, ct, l in parts:
+        pcmm.copy_columns(batch, L, off, ct, l, 0, l, 8 * n)
+        off += l
+    # The packed batch holds each part's ciphertexts in its column range.
+    torch.cuda.synchronize()
+    packed = pcmm.planar_to_ct(pcmm.to_host_words(batch), n * L).reshape(n, L, 2, 16)
+    off = 0
+    for pr, ct, l in parts:
+        one = pcmm.planar_to_ct(pcmm.to_host_words(ct), n * l).reshape(n, l, 2, 16)
+        assert (packed[:, off:off + l] == one).all()
+        # Split back.
+        back = torch.empty_like(ct)
+        pcmm.copy_columns(back, l, 0, batch, L, off, l, 8 * n)
+        torch.cuda.synchronize()
+        assert torch.equal(back, ct)
+        off += l
