@@ -48,6 +48,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-schoolbook", action="store_true")
+    ap.add_argument("--workload", choices=["large", "serving", "batched"], default="large",
+                    help="large: the single large PC-MM (the headline line); serving: Poisson "
+                         "request sweep of encrypted linear layers; batched: 64 uneven instances")
+    ap.add_argument("--rates", default="10,20,50,100,200,500,1000,2000")
+    ap.add_argument("--seconds", type=float, default=2.0, help="arrival window per rate (serving)")
     return ap.parse_args()
 
 
@@ -369,11 +374,191 @@ def run_ours(args, dist):
     }
 
 
+def run_batched(args, dist):
+    """64 independent PC-MM instances (m, n, l uniform in [32, 768], w uniform
+    in {1..8}, 8-bit messages): strip widths from the autotuner, all instances
+    in one persistent launch replayed from a CUDA graph, against one plain
+    pcmm_cussen launch per instance on the same GPU."""
+    import torch
+
+    from paper_2504_14497_gb300 import autotune, build, counts, inputs, pcmm
+
+    build.build()
+    torch.cuda.set_device(dist.local)
+    dev = torch.device("cuda", dist.local)
+    pcmm.init(dist.local)
+    shapes = inputs.batched_shapes(SEED + 2, count=64)
+    st = inputs.streams(SEED + 2)
+    sk = inputs.uniform_scalars(st["sk"], (1,))[0]
+    tab = pcmm.keytable(pcmm.public_key(sk, device=dev), device=dev)
+    cache = {}
+    items, ops = [], 0
+    t_tune = time.perf_counter()
+    for i, (m, n, l, w) in enumerate(shapes):
+        k = autotune.tune(m, n, l, w, device=dev, cache=cache)
+        A_h = st["A"].integers(0, 1 << w, size=(m, n), dtype=np.uint8)
+        msg = st["B"].integers(0, 256, size=(n * l,), dtype=np.uint8)
+        r = inputs.uniform_scalars(st["r"], (n * l,))
+        ctB = pcmm.encrypt(tab, torch.from_numpy(msg).to(dev), pcmm.to_device_words(pcmm.scalars_to_planar(r), dev))
+        items.append((torch.from_numpy(A_h).to(dev), ctB, l, w, k))
+        ops += counts.point_ops(counts.cussen_counts(A_h, w, k, l))
+    t_tune = time.perf_counter() - t_tune
+    torch.cuda.synchronize()
+    batch = pcmm.Batch(items)
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 1)):
+            batch.run()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            batch.run()
+    torch.cuda.synchronize()
+    if pcmm.workspace_status(batch.ws) != 0:
+        raise RuntimeError("batched run reported a device error")
+    cur = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(cur)
+    for _ in range(args.steps):
+        g.replay()
+    e1.record(cur)
+    e1.synchronize()
+    ms_batched = e0.elapsed_time(e1) / args.steps
+    if pcmm.workspace_status(batch.ws) != 0:
+        raise RuntimeError("batched run reported a device error")
+    # One plain launch per instance (plan + tables + gather each), same k.
+    wss = [pcmm.workspace(A.shape[0], A.shape[1], l, w, k, device=dev) for A, _, l, w, k in items]
+    outs = [torch.empty(48 * A.shape[0] * l, dtype=torch.int32, device=dev) for A, _, l, w, k in items]
+
+    def plain():
+        for (A, ctB, l, w, k), ws, out in zip(items, wss, outs):
+            pcmm.cussen(A, ctB, l, w, k=k, ws=ws, out=out)
+
+    plain()
+    torch.cuda.synchronize()
+    e0.record(cur)
+    for _ in range(args.steps):
+        plain()
+    e1.record(cur)
+    e1.synchronize()
+    ms_plain = e0.elapsed_time(e1) / args.steps
+    same = all(torch.equal(pcmm.normalize(o, A.shape[0] * l), pcmm.normalize(b, A.shape[0] * l))
+               for o, b, (A, _, l, _, _) in zip(outs, batch.outs, items))
+    return {"workload": "batched: 64 PC-MM instances, m,n,l ~ U[32,768], w ~ U{1..8}, 8-bit messages, "
+                        "one persistent launch replayed from a CUDA graph",
+            "metric": "point-adds/s (batched) vs one launch per instance", "unit": "point-adds/s",
+            "value": ops / (ms_batched / 1e3), "ms_per_batch": ms_batched,
+            "plain_value": ops / (ms_plain / 1e3), "plain_ms_per_batch": ms_plain,
+            "speedup_vs_plain": ms_plain / ms_batched, "point_ops_per_batch": ops,
+            "outputs_identical": bool(same), "k": [it[4] for it in items],
+            "autotune_s": t_tune, "steps": args.steps, "n_gpus": 1}
+
+
+SERVING_MODELS = {"mlp_784": (256, 784), "mlp_256": (128, 256), "mlp_out": (10, 128)}
+
+
+def run_serving(args, dist):
+    """Encrypted linear-layer serving: Poisson arrivals over three resident
+    models (4-bit weights), input batches of 1..64 encrypted column vectors
+    (8-bit messages).  Continuous batching against one plain pcmm_cussen
+    launch per request (plan rebuilt every time, one request at a time)."""
+    import torch
+
+    from paper_2504_14497_gb300 import counts, inputs, pcmm
+    from paper_2504_14497_gb300.serving import GpuBackend, Request, Server
+
+    rng = np.random.default_rng(SEED + 3)
+    st = inputs.streams(SEED + 3)
+    be = GpuBackend(f"cuda:{dist.local}", max_inflight=8)
+    dev = be.device
+    weights = {nm: (st["A"].integers(0, 16, size=shape, dtype=np.uint8), 4, 0)
+               for nm, shape in SERVING_MODELS.items()}
+    srv_proto = dict(hbm_budget=40e9, max_inflight=8, max_batch_cols=256)
+    sk = inputs.uniform_scalars(st["sk"], (1,))[0]
+    tab = pcmm.keytable(pcmm.public_key(sk, device=dev), device=dev)
+    pool = []                                   # (model, l, ct) encrypted inputs
+    for nm, (m, n) in SERVING_MODELS.items():
+        for _ in range(6):
+            l = int(rng.integers(1, 65))
+            msg = st["B"].integers(0, 256, size=(n * l,), dtype=np.uint8)
+            r = inputs.uniform_scalars(st["r"], (n * l,))
+            ct = pcmm.encrypt(tab, torch.from_numpy(msg).to(dev),
+                              pcmm.to_device_words(pcmm.scalars_to_planar(r), dev))
+            pool.append((nm, l, ct))
+    torch.cuda.synchronize()
+    k_of = {nm: pcmm.choose_k(m, n, 256, 4) for nm, (m, n) in SERVING_MODELS.items()}
+    ops_of = {}
+    for nm, l, _ in pool:
+        key = (nm, l)
+        if key not in ops_of:
+            ops_of[key] = counts.point_ops(counts.cussen_counts(weights[nm][0], 4, k_of[nm], l))
+
+    def arrivals(rate):
+        nreq = max(20, int(rate * args.seconds))
+        t = np.cumsum(rng.exponential(1.0 / rate, size=nreq))
+        picks = rng.integers(0, len(pool), size=nreq)
+        return [(float(ti), pool[int(p)]) for ti, p in zip(t, picks)]
+
+    def summarise(lat, first, last, ops):
+        lat = sorted(lat)
+        pct = lambda q: lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
+        span = max(last - first, 1e-9)
+        return {"p50_ms": 1e3 * pct(0.5), "p99_ms": 1e3 * pct(0.99), "req_per_s": len(lat) / span,
+                "point_adds_per_s": ops / span, "requests": len(lat)}
+
+    rates = [float(x) for x in args.rates.split(",")]
+    out_rates = []
+    warm = Server(be, weights, **srv_proto)
+    warm.run([Request(i, nm, ct, l, arrival=0.0) for i, (nm, l, ct) in enumerate(pool)])
+    for rate in rates:
+        arr = arrivals(rate)
+        # Continuous batching.
+        srv = Server(be, weights, **srv_proto)
+        reqs = [Request(i, nm, ct, l, arrival=t) for i, (t, (nm, l, ct)) in enumerate(arr)]
+        srv.run(reqs)
+        ops = sum(ops_of[(r.model, r.l)] for r in srv.completed)
+        cb = summarise([r.latency for r in srv.completed], min(r.arrival for r in reqs),
+                       max(r.finish for r in srv.completed), ops)
+        cb["batches"] = srv.stats()["batches"]
+        # One plain launch per request, in arrival order.
+        plain_A = {nm: torch.from_numpy(weights[nm][0]).to(dev) for nm in SERVING_MODELS}
+        ws_cache = {}
+        lat, t0 = [], time.perf_counter()
+        for t, (nm, l, ct) in arr:
+            while time.perf_counter() - t0 < t:
+                pass
+            m, n = SERVING_MODELS[nm]
+            key = (nm, l)
+            if key not in ws_cache:
+                ws_cache[key] = pcmm.workspace(m, n, l, 4, k_of[nm], device=dev)
+            jac = pcmm.cussen(plain_A[nm], ct, l, 4, k=k_of[nm], ws=ws_cache[key])
+            pcmm.normalize(jac, m * l)
+            torch.cuda.synchronize()
+            lat.append(time.perf_counter() - t0 - t)
+        last = time.perf_counter() - t0
+        ops_p = sum(ops_of[(nm, l)] for _, (nm, l, _) in arr)
+        pl = summarise(lat, arr[0][0], last, ops_p)
+        out_rates.append({"rate": rate, "continuous_batching": cb, "one_launch_per_request": pl})
+    return {"workload": "serving: Poisson encrypted linear layers over models "
+                        + ", ".join(f"{m}x{n}" for m, n in SERVING_MODELS.values())
+                        + " (4-bit weights), inputs of 1..64 encrypted columns, HBM budget 40 GB",
+            "metric": "p50/p99 latency and requests/s per arrival rate", "n_gpus": 1,
+            "rates": out_rates}
+
+
 def main():
     args = parse()
     dist = Dist(args.gpus)
     try:
-        out = run_reference(args, dist) if args.impl == "reference" else run_ours(args, dist)
+        if args.impl == "reference":
+            out = run_reference(args, dist)
+        elif args.workload == "serving":
+            out = run_serving(args, dist)
+        elif args.workload == "batched":
+            out = run_batched(args, dist)
+        else:
+            out = run_ours(args, dist)
         if dist.rank == 0 and out is not None:
             print(json.dumps(out), flush=True)
     finally:

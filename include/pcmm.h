@@ -198,6 +198,58 @@ pcmm_status pcmm_cussen_execute(const void *plan, int m, int n, int w, int k, co
 pcmm_status pcmm_cussen_static(const uint8_t *A, int m, int n, int w, const uint32_t *ctB, int l,
                                uint32_t *ctC, int k, pcmm_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Batched PC-MM: many Cussen instances of different shapes and bit-widths
+ * in one persistent kernel launch.
+ * ---------------------------------------------------------------------- */
+
+/* One instance: A (device uint8 m x n, entries < 2^w), ctB (device affine
+ * ciphertext matrix n x l), ctC (device Jacobian output m x l), strip width
+ * k (0: pcmm_cussen_choose_k).  Outputs must not overlap each other or any
+ * input. */
+typedef struct {
+    const uint8_t *A;
+    int m, n, w;
+    const uint32_t *ctB;
+    int l;
+    uint32_t *ctC;
+    int k;
+} pcmm_problem;
+
+/* Launch description written by pcmm_batched_prepare (caller-owned POD). */
+typedef struct {
+    int count, nsegs;
+    long long ntasks, nstrips;
+    int nctrs, grid;
+    size_t off_insts, off_segs, off_map, off_ctrs, off_scratch, scratch_u4, bytes;
+} pcmm_batch_info;
+
+/* Workspace bytes for a batch on the current device (0 for invalid input).
+ * max_strips: strips per pass of an instance (its column strips are built and
+ * gathered max_strips at a time, two passes' tables resident); 0 = 64. */
+size_t pcmm_batched_workspace_bytes(const pcmm_problem *probs, int count, int max_strips);
+
+/* Sizes every instance, lays out the workspace (plans, two table buffers per
+ * instance, per-warp scratch, counters) and uploads the instance descriptors
+ * and the task schedule; synchronises `stream` before returning.  The
+ * problems' pointers are baked in: rerun pcmm_batched_prepare when they
+ * change.  probs: host array of count problems.  max_strips: as for
+ * pcmm_batched_workspace_bytes (same value).  ws: device, 256-byte
+ * aligned, >= pcmm_batched_workspace_bytes.  info: host, written.
+ * Errors: PCMM_EINVAL, PCMM_ENOMEM, PCMM_ECUDA. */
+pcmm_status pcmm_batched_prepare(const pcmm_problem *probs, int count, int max_strips, void *ws,
+                                 size_t ws_bytes, pcmm_batch_info *info, pcmm_stream_t stream);
+
+/* Runs a prepared batch: resets the queue and counters (two memsets),
+ * builds the plans of all instances (one launch) and runs every table build
+ * and gather in ONE persistent kernel whose warps pull tasks from a device
+ * queue.  Enqueues a fixed sequence of operations, so it may be captured in a
+ * CUDA graph and replayed.  Dependency waits inside the kernel are bounded:
+ * if one gives up (about a second), bit 4 of the status word (first 4 bytes
+ * of ws, pcmm_workspace_status) is set and the results are invalid.
+ * Errors: PCMM_EINVAL, PCMM_ECUDA. */
+pcmm_status pcmm_batched_run(const pcmm_batch_info *info, void *ws, pcmm_stream_t stream);
+
 /* Reads the status word of a pcmm_cussen workspace into *status_host after
  * synchronising `stream`.  0 means no kernel raised an error bit. */
 pcmm_status pcmm_workspace_status(const void *ws, uint32_t *status_host, pcmm_stream_t stream);

@@ -1,0 +1,84 @@
+"""Strip-width autotuner for Cussen PC-MM.
+
+For a problem shape (m, n, l, w) it times ``pcmm_cussen`` on the device for
+the strip widths around the library's cost-model choice and keeps the
+fastest.  Inputs are synthetic (uniform w-bit A, random words for the ciphertext
+coordinates): the kernels' work depends on the distinct values of A, not on
+the points.  Results are cached in a JSON file (``PCMM_AUTOTUNE_CACHE``
+or the path given) keyed by ``"m,n,l,w"``.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import numpy as np
+
+from . import pcmm
+
+def candidates(m: int, n: int, l: int, w: int) -> list:
+    kmax = max(1, min(12 // w, n))
+    k0 = pcmm.choose_k(m, n, l, w)
+    ks = {k for k in (k0 - 1, k0, k0 + 1, k0 + 2) if 1 <= k <= kmax}
+    return sorted(ks)
+
+
+def _cache_path(path=None):
+    return path or os.environ.get("PCMM_AUTOTUNE_CACHE")
+
+
+def load_cache(path=None) -> dict:
+    p = _cache_path(path)
+    if p and os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+def save_cache(cache: dict, path=None):
+    p = _cache_path(path)
+    if p:
+        tmp = p + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+        os.replace(tmp, p)
+
+
+def _synthetic(m, n, l, w, device, seed=0):
+    import torch
+
+    rng = np.random.default_rng(seed)
+    A = torch.from_numpy(rng.integers(0, 1 << w, size=(m, n), dtype=np.uint8)).to(device)
+    words = rng.integers(0, 1 << 32, size=(32 * n * l,), dtype=np.uint64).astype(np.uint32)
+    ctB = pcmm.to_device_words(words, device)
+    return A, ctB
+
+
+def tune(m: int, n: int, l: int, w: int, device="cuda", reps: int = 2, cache=None, path=None) -> int:
+    """Best strip width for the shape (measured, cached)."""
+    import torch
+
+    key = f"{m},{n},{l},{w}"
+    cache = load_cache(path) if cache is None else cache
+    if key in cache:
+        return int(cache[key]["k"])
+    A, ctB = _synthetic(m, n, l, w, device)
+    out = torch.empty(48 * m * l, dtype=torch.int32, device=device)
+    times = {}
+    for k in candidates(m, n, l, w):
+        ws = pcmm.workspace(m, n, l, w, k, device=device)
+        pcmm.cussen(A, ctB, l, w, k=k, ws=ws, out=out)
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            pcmm.cussen(A, ctB, l, w, k=k, ws=ws, out=out)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        times[k] = best
+        del ws
+    k_best = min(times, key=times.get)
+    cache[key] = {"k": int(k_best), "ms": {str(k): t for k, t in times.items()}}
+    save_cache(cache, path)
+    return int(k_best)

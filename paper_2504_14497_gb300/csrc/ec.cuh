@@ -192,6 +192,24 @@ __device__ __forceinline__ void load_aff(aff& Q, const uint4* __restrict__ base,
     fe_from_quads(Q.y, q2, q3);
 }
 
+// L2-only loads (ld.global.cg), for data written by other SMs during the
+// same kernel launch.
+__device__ __forceinline__ void load_aff_cg(aff& Q, const uint4* __restrict__ base, size_t stride, size_t i) {
+    uint4 q0 = __ldcg(base + i), q1 = __ldcg(base + stride + i), q2 = __ldcg(base + 2 * stride + i),
+          q3 = __ldcg(base + 3 * stride + i);
+    fe_from_quads(Q.x, q0, q1);
+    fe_from_quads(Q.y, q2, q3);
+}
+
+__device__ __forceinline__ void load_jac_cg(jac& P, const uint4* __restrict__ base, size_t stride, size_t i) {
+    uint4 q0 = __ldcg(base + i), q1 = __ldcg(base + stride + i), q2 = __ldcg(base + 2 * stride + i);
+    uint4 q3 = __ldcg(base + 3 * stride + i), q4 = __ldcg(base + 4 * stride + i),
+          q5 = __ldcg(base + 5 * stride + i);
+    fe_from_quads(P.X, q0, q1);
+    fe_from_quads(P.Y, q2, q3);
+    fe_from_quads(P.Z, q4, q5);
+}
+
 __device__ __forceinline__ void store_aff(uint4* __restrict__ base, size_t stride, size_t i, const aff& Q) {
     base[i] = fe_lo(Q.x);
     base[stride + i] = fe_hi(Q.x);

@@ -1,0 +1,361 @@
+// Many Cussen PC-MM instances of uneven shapes and bit-widths in one
+// persistent launch.
+//
+// pcmm_batched_prepare (host) sizes every instance (strip width k from the
+// caller or the cost model; S strips per pass), lays out the workspace and
+// uploads the instance descriptors and the schedule.  pcmm_batched_run then
+// enqueues only fixed-size work: two memsets, the plans of all instances
+// (one launch, one block per strip) and ONE persistent kernel, so it can be
+// captured in a CUDA graph and replayed.
+//
+// The persistent kernel's warps pull tasks from a device-wide queue (an
+// atomic counter).  The schedule is a list of segments in round order: in
+// round r, the table-build tasks of every instance's r-th pass of strips,
+// then the gather tasks of those passes.  A task may wait (bounded spin) only
+// on tasks earlier in the queue:
+//   * a gather task of pass r waits for all table tasks of that pass and for
+//     all gather tasks of pass r - 1 (they update the same outputs);
+//   * a table task of pass r waits for all gather tasks of pass r - 2 (the
+//     two table buffers of an instance alternate between passes).
+// Every task a warp waits on was pulled earlier by a warp that is running and
+// only waits on even earlier tasks, so the queue always progresses.  A wait
+// that exceeds its bound (about one second) sets a status bit and the warps
+// stop pulling tasks instead of hanging.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "cussen_core.cuh"
+#include "profiler.cuh"
+
+using namespace pcmm;
+using namespace pcmm::cussen;
+
+namespace {
+
+constexpr uint32_t DEV_ERR_TIMEOUT = 1u << 2;
+constexpr int TASK_TABLE = 0, TASK_GATHER = 1;
+constexpr int BATCH_THREADS = 128;
+
+struct Inst {
+    const uint4* ctB;
+    uint4* ctC;
+    const uint8_t* A;
+    PlanPtrs P;
+    uint4* tables;              // two buffers of 4 * table_points uint4
+    size_t table_points;        // points per buffer (S strips)
+    size_t item_u4;
+    int m, n, l, w, k;
+    int nstrips, n1max, l2max, emax, lp, njb;
+    int S, nchunks;
+    int ctr_base;               // 2 counters per pass: tables done, gathers done
+};
+
+struct Segment {
+    long long start;            // first task index of the segment
+    int type, inst, chunk, count;
+};
+
+struct BatchHeader {            // device copy, first bytes of the workspace
+    uint32_t status;
+    int head;                   // next task index
+};
+
+__device__ __forceinline__ bool wait_at_least(const int* ctr, int target, uint32_t* status) {
+    for (int it = 0; it < (1 << 22); it++) {
+        if (*(volatile const int*)ctr >= target) {
+            __threadfence();
+            return true;
+        }
+        if (*(volatile const uint32_t*)status & DEV_ERR_TIMEOUT) return false;
+        __nanosleep(256);
+    }
+    atomicOr(status, DEV_ERR_TIMEOUT);
+    return false;
+}
+
+__global__ void __launch_bounds__(PLAN_THREADS) batched_plan_kernel(const Inst* __restrict__ insts,
+                                                                    const int2* __restrict__ strip_map) {
+    const int2 is = strip_map[blockIdx.x];
+    const Inst& I = insts[is.x];
+    plan_strip(I.A, I.m, I.n, I.w, I.k, I.emax, I.P, is.y);
+}
+
+__global__ void __launch_bounds__(BATCH_THREADS) batched_kernel(const Inst* __restrict__ insts,
+                                                                const Segment* __restrict__ segs, int nsegs,
+                                                                long long ntasks, BatchHeader* hdr,
+                                                                int* ctrs, uint4* scratch,
+                                                                size_t scratch_u4) {
+    const unsigned lane = threadIdx.x & 31u;
+    const long long warp_id = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    uint4* my_scratch = scratch + (size_t)warp_id * scratch_u4;
+    for (;;) {
+        long long t = 0;
+        if (lane == 0) t = atomicAdd(&hdr->head, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= ntasks) break;
+        if (*(volatile uint32_t*)&hdr->status & DEV_ERR_TIMEOUT) break;
+        // Segment holding task t (segments are sorted by start).
+        int lo = 0, hi = nsegs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (segs[mid].start <= t) lo = mid; else hi = mid - 1;
+        }
+        const Segment sg = segs[lo];
+        const long long item = t - sg.start;
+        const Inst& I = insts[sg.inst];
+        const int s0 = sg.chunk * I.S;
+        const int sc = min(I.S, I.nstrips - s0);
+        uint4* tbuf = I.tables + (size_t)(sg.chunk & 1) * 4 * I.table_points;
+        int* tdone = ctrs + I.ctr_base + 2 * sg.chunk;
+        bool ok = true;
+        if (sg.type == TASK_TABLE) {
+            if (sg.chunk >= 2 && lane == 0)
+                ok = wait_at_least(tdone - 4 + 1, I.m * 2 * I.njb, &hdr->status);
+            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+            TableArgs ta;
+            ta.ctB = I.ctB;
+            ta.A = nullptr;
+            ta.m = I.m; ta.n = I.n; ta.l = I.l; ta.w = I.w; ta.k = I.k;
+            ta.lp = I.lp; ta.njb = I.njb; ta.n1max = I.n1max; ta.l2max = I.l2max; ta.emax = I.emax;
+            ta.s0 = s0; ta.nstrips_chunk = sc;
+            ta.scratch = my_scratch;
+            ta.item_u4 = I.item_u4;
+            ta.table = tbuf;
+            ta.table_points = I.table_points;
+            table_item(ta, I.P, item, my_scratch);
+            __syncwarp();
+            __threadfence();
+            if (lane == 0) atomicAdd(tdone, 1);
+        } else {
+            if (lane == 0) {
+                ok = wait_at_least(tdone, sc * 2 * I.njb, &hdr->status);
+                if (ok && sg.chunk > 0) ok = wait_at_least(tdone - 2 + 1, I.m * 2 * I.njb, &hdr->status);
+            }
+            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+            GatherArgs ga;
+            ga.m = I.m; ga.l = I.l; ga.lp = I.lp; ga.njb = I.njb; ga.emax = I.emax;
+            ga.s0 = s0; ga.nstrips_chunk = sc;
+            ga.first = (sg.chunk == 0);
+            ga.table = tbuf;
+            ga.table_points = I.table_points;
+            ga.ctC = I.ctC;
+            gather_item<true>(ga, I.P, item);
+            __syncwarp();
+            __threadfence();
+            if (lane == 0) atomicAdd(tdone + 1, 1);
+        }
+    }
+}
+
+struct HostLayout {
+    std::vector<Inst> insts;
+    std::vector<Segment> segs;
+    std::vector<int2> strip_map;
+    long long ntasks = 0;
+    size_t off_insts = 0, off_segs = 0, off_map = 0, off_ctrs = 0, off_scratch = 0, bytes = 0;
+    int nctrs = 0;
+    size_t scratch_u4 = 0;
+    int grid = 0;
+};
+
+// Strips per pass of one instance: at most max_strips (long gathers), and
+// few enough that the two table buffers stay near `table_budget` bytes.
+int strips_per_pass(const Layout& L, size_t table_budget, int max_strips) {
+    const size_t per_strip = align256(L.table_points_per_strip * 64);
+    size_t S = table_budget / (2 * per_strip);
+    if (S > (size_t)max_strips) S = max_strips;
+    if (S > (size_t)L.nstrips) S = L.nstrips;
+    return S < 1 ? 1 : (int)S;
+}
+
+pcmm_status build_layout(const pcmm_problem* probs, int count, int max_strips, int grid,
+                         HostLayout& H) {
+    if (!probs || count < 1 || grid < 1 || max_strips < 0) return PCMM_EINVAL;
+    if (max_strips == 0) max_strips = 64;
+    H = HostLayout();
+    H.grid = grid;
+    std::vector<Layout> Ls(count);
+    size_t off = 256;
+    for (int i = 0; i < count; i++) {
+        const pcmm_problem& p = probs[i];
+        if (!p.A || !p.ctB || !p.ctC) return PCMM_EINVAL;
+        int k = p.k ? p.k : pcmm_cussen_choose_k(p.m, p.n, p.l, p.w);
+        if (!make_layout(Ls[i], p.m, p.n, p.l, p.w, k)) return PCMM_EINVAL;
+    }
+    // Plans.
+    std::vector<size_t> plan_off(count);
+    for (int i = 0; i < count; i++) {
+        plan_off[i] = off;
+        off = align256(off + Ls[i].plan_bytes);
+    }
+    // Table buffers (two per instance).
+    const size_t table_budget = (size_t)256 << 20;
+    std::vector<size_t> tab_off(count);
+    H.insts.resize(count);
+    int ctr = 0;
+    for (int i = 0; i < count; i++) {
+        const Layout& L = Ls[i];
+        Inst& I = H.insts[i];
+        I.S = strips_per_pass(L, table_budget, max_strips);
+        I.nchunks = (L.nstrips + I.S - 1) / I.S;
+        I.table_points = (size_t)I.S * L.table_points_per_strip;
+        tab_off[i] = off;
+        off = align256(off + 2 * I.table_points * 64);
+        I.ctr_base = ctr;
+        ctr += 2 * I.nchunks;
+        I.m = L.m; I.n = L.n; I.l = L.l; I.w = L.w; I.k = L.k;
+        I.nstrips = L.nstrips; I.n1max = L.n1max; I.l2max = L.l2max; I.emax = L.emax;
+        I.lp = L.lp; I.njb = L.njb; I.item_u4 = L.item_u4;
+        H.scratch_u4 = std::max(H.scratch_u4, L.item_u4);
+    }
+    H.nctrs = ctr;
+    // Schedule: rounds of passes; within a round, larger instances first.
+    int rounds = 0;
+    for (auto& I : H.insts) rounds = std::max(rounds, I.nchunks);
+    std::vector<int> order(count);
+    for (int i = 0; i < count; i++) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int a, int b) {
+        const double wa = (double)H.insts[a].m * H.insts[a].l * H.insts[a].nstrips;
+        const double wb = (double)H.insts[b].m * H.insts[b].l * H.insts[b].nstrips;
+        return wa > wb;
+    });
+    long long t = 0;
+    for (int r = 0; r < rounds; r++) {
+        for (int ph = 0; ph < 2; ph++) {
+            for (int i : order) {
+                const Inst& I = H.insts[i];
+                if (r >= I.nchunks) continue;
+                const int sc = std::min(I.S, I.nstrips - r * I.S);
+                Segment sg;
+                sg.start = t;
+                sg.type = ph == 0 ? TASK_TABLE : TASK_GATHER;
+                sg.inst = i;
+                sg.chunk = r;
+                sg.count = ph == 0 ? sc * 2 * I.njb : I.m * 2 * I.njb;
+                H.segs.push_back(sg);
+                t += sg.count;
+            }
+        }
+    }
+    H.ntasks = t;
+    // The queue head is a 32-bit counter that every warp bumps once past the end.
+    if (H.ntasks + (long long)grid * (BATCH_THREADS / 32) >= (1LL << 31)) return PCMM_EUNSUPPORTED;
+    for (int i = 0; i < count; i++)
+        for (int s = 0; s < H.insts[i].nstrips; s++) H.strip_map.push_back(make_int2(i, s));
+    H.off_insts = off;   off = align256(off + sizeof(Inst) * count);
+    H.off_segs = off;    off = align256(off + sizeof(Segment) * H.segs.size());
+    H.off_map = off;     off = align256(off + sizeof(int2) * H.strip_map.size());
+    H.off_ctrs = off;    off = align256(off + sizeof(int) * (size_t)H.nctrs);
+    H.off_scratch = off; off = align256(off + (size_t)grid * (BATCH_THREADS / 32) * H.scratch_u4 * 16);
+    H.bytes = off;
+    // Device pointers are filled in by prepare once the workspace is known.
+    for (int i = 0; i < count; i++) {
+        H.insts[i].A = probs[i].A;
+        H.insts[i].ctB = (const uint4*)probs[i].ctB;
+        H.insts[i].ctC = (uint4*)probs[i].ctC;
+        H.insts[i].P.status = nullptr;
+        H.insts[i].tables = (uint4*)(uintptr_t)tab_off[i];   // offset for now
+        H.insts[i].P.rank = (uint16_t*)(uintptr_t)plan_off[i];  // offset for now
+    }
+    // Keep the per-instance Layouts' plan offsets for prepare.
+    for (int i = 0; i < count; i++) {
+        PlanPtrs P = plan_ptrs(Ls[i], (void*)(uintptr_t)plan_off[i]);
+        H.insts[i].P = P;
+    }
+    return PCMM_OK;
+}
+
+int resident_grid() {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel, BATCH_THREADS, 0) !=
+        cudaSuccess)
+        return 0;
+    return sms * std::max(per_sm, 1);
+}
+
+}  // namespace
+
+extern "C" size_t pcmm_batched_workspace_bytes(const pcmm_problem* probs, int count, int max_strips) {
+    const int grid = resident_grid();
+    if (grid <= 0) return 0;
+    HostLayout H;
+    if (build_layout(probs, count, max_strips, grid, H) != PCMM_OK) return 0;
+    return H.bytes;
+}
+
+extern "C" pcmm_status pcmm_batched_prepare(const pcmm_problem* probs, int count, int max_strips, void* ws,
+                                            size_t ws_bytes, pcmm_batch_info* info, pcmm_stream_t stream) {
+    if (!ws || !info || ((uintptr_t)ws & 255u)) return PCMM_EINVAL;
+    const int grid = resident_grid();
+    if (grid <= 0) return PCMM_ECUDA;
+    HostLayout H;
+    pcmm_status rc = build_layout(probs, count, max_strips, grid, H);
+    if (rc != PCMM_OK) return rc;
+    if (ws_bytes < H.bytes) return PCMM_ENOMEM;
+    uint8_t* base = (uint8_t*)ws;
+    for (auto& I : H.insts) {
+        I.tables = (uint4*)(base + (uintptr_t)I.tables);
+        PlanPtrs& P = I.P;
+        const uintptr_t b = (uintptr_t)base;
+        P.rank = (uint16_t*)(b + (uintptr_t)P.rank);
+        P.nent = (int32_t*)(b + (uintptr_t)P.nent);
+        P.codes = (uint16_t*)(b + (uintptr_t)P.codes);
+        P.col_len = (uint16_t*)(b + (uintptr_t)P.col_len);
+        P.col_vN = (uint8_t*)(b + (uintptr_t)P.col_vN);
+        P.col_ptr = (uint8_t*)(b + (uintptr_t)P.col_ptr);
+        P.col_rank1 = (uint8_t*)(b + (uintptr_t)P.col_rank1);
+        P.status = (uint32_t*)base;        // all instances report into the batch status word
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(base + H.off_insts, H.insts.data(), sizeof(Inst) * H.insts.size(),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(base + H.off_segs, H.segs.data(), sizeof(Segment) * H.segs.size(),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(base + H.off_map, H.strip_map.data(), sizeof(int2) * H.strip_map.size(),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return PCMM_ECUDA;
+    // The host vectors die on return: wait for the copies.
+    if (cudaStreamSynchronize(st) != cudaSuccess) return PCMM_ECUDA;
+    info->count = count;
+    info->nsegs = (int)H.segs.size();
+    info->ntasks = H.ntasks;
+    info->nstrips = (long long)H.strip_map.size();
+    info->nctrs = H.nctrs;
+    info->grid = H.grid;
+    info->off_insts = H.off_insts;
+    info->off_segs = H.off_segs;
+    info->off_map = H.off_map;
+    info->off_ctrs = H.off_ctrs;
+    info->off_scratch = H.off_scratch;
+    info->scratch_u4 = H.scratch_u4;
+    info->bytes = H.bytes;
+    return PCMM_OK;
+}
+
+extern "C" pcmm_status pcmm_batched_run(const pcmm_batch_info* info, void* ws, pcmm_stream_t stream) {
+    if (!info || !ws || ((uintptr_t)ws & 255u) || info->grid < 1 || info->nstrips < 1) return PCMM_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint8_t* base = (uint8_t*)ws;
+    if (cudaMemsetAsync(base, 0, sizeof(BatchHeader), st) != cudaSuccess ||
+        cudaMemsetAsync(base + info->off_ctrs, 0, sizeof(int) * (size_t)info->nctrs, st) != cudaSuccess)
+        return PCMM_ECUDA;
+    const Inst* insts = (const Inst*)(base + info->off_insts);
+    {
+        ProfScope ps(KID_PLAN, st);
+        batched_plan_kernel<<<(unsigned)info->nstrips, PLAN_THREADS, 0, st>>>(
+            insts, (const int2*)(base + info->off_map));
+    }
+    PCMM_CUDA_CHECK_LAUNCH();
+    {
+        ProfScope ps(KID_BATCHED, st);
+        batched_kernel<<<(unsigned)info->grid, BATCH_THREADS, 0, st>>>(
+            insts, (const Segment*)(base + info->off_segs), info->nsegs, info->ntasks, (BatchHeader*)base,
+            (int*)(base + info->off_ctrs), (uint4*)(base + info->off_scratch), info->scratch_u4);
+    }
+    PCMM_CUDA_CHECK_LAUNCH();
+    return PCMM_OK;
+}

@@ -13,7 +13,8 @@ enum KernelId {
     KID_ENCRYPT = 4,
     KID_SCHOOLBOOK = 5,
     KID_COMB = 6,
-    KID_COUNT = 7
+    KID_BATCHED = 7,
+    KID_COUNT = 8
 };
 
 // Records a start event on construction and a stop event on destruction

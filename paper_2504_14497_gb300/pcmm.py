@@ -27,7 +27,8 @@ EXPORTS = (
     "pcmm_version", "pcmm_status_string", "pcmm_init", "pcmm_keytable_bytes", "pcmm_keytable",
     "pcmm_encrypt", "pcmm_base_mul", "pcmm_schoolbook", "pcmm_cussen_choose_k", "pcmm_cussen_workspace_bytes",
     "pcmm_cussen", "pcmm_cussen_plan_bytes", "pcmm_cussen_plan", "pcmm_cussen_exec_bytes",
-    "pcmm_cussen_execute", "pcmm_workspace_status", "pcmm_copy_columns", "pcmm_normalize", "pcmm_profile_enable",
+    "pcmm_cussen_execute", "pcmm_batched_workspace_bytes", "pcmm_batched_prepare", "pcmm_batched_run",
+    "pcmm_workspace_status", "pcmm_copy_columns", "pcmm_normalize", "pcmm_profile_enable",
     "pcmm_profile_read", "pcmm_kernel_count", "pcmm_kernel_name", "pcmm_test_field", "pcmm_test_point",
 )
 
@@ -259,6 +260,59 @@ def cussen(A, ctB, l: int, w: int, k: int = 0, ws=None, out=None, stream=None):
     _check(lib().pcmm_cussen(_ptr(A), m, n, w, _ptr(ctB), l, _ptr(out), k, _ptr(ws), ws.numel(),
                              _stream(stream)), "pcmm_cussen")
     return out
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("m", ctypes.c_int), ("n", ctypes.c_int), ("w", ctypes.c_int),
+                ("ctB", ctypes.c_void_p), ("l", ctypes.c_int), ("ctC", ctypes.c_void_p), ("k", ctypes.c_int)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int), ("nsegs", ctypes.c_int), ("ntasks", ctypes.c_longlong),
+                ("nstrips", ctypes.c_longlong), ("nctrs", ctypes.c_int), ("grid", ctypes.c_int),
+                ("off_insts", ctypes.c_size_t), ("off_segs", ctypes.c_size_t), ("off_map", ctypes.c_size_t),
+                ("off_ctrs", ctypes.c_size_t), ("off_scratch", ctypes.c_size_t),
+                ("scratch_u4", ctypes.c_size_t), ("bytes", ctypes.c_size_t)]
+
+
+class Batch:
+    """A prepared batch of Cussen PC-MM instances (one persistent launch).
+
+    items: list of (A cuda uint8 [m, n], ctB cuda int32, l, w, k); outputs are
+    allocated here (Jacobian, ``self.outs``)."""
+
+    def __init__(self, items, max_strips: int = 0, stream=None):
+        torch = _torch()
+        L = lib()
+        L.pcmm_batched_workspace_bytes.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+        L.pcmm_batched_workspace_bytes.restype = ctypes.c_size_t
+        L.pcmm_batched_prepare.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                           ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p]
+        L.pcmm_batched_prepare.restype = ctypes.c_int
+        L.pcmm_batched_run.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        L.pcmm_batched_run.restype = ctypes.c_int
+        self.items = list(items)
+        n = len(self.items)
+        self.probs = (Problem * n)()
+        self.outs = []
+        for i, (A, ctB, l, w, k) in enumerate(self.items):
+            m, nn = A.shape
+            out = torch.empty(PCMM_JAC_WORDS * m * l, dtype=torch.int32, device=A.device)
+            self.outs.append(out)
+            self.probs[i] = Problem(A.data_ptr(), m, nn, w, ctB.data_ptr(), l, out.data_ptr(), k)
+        self.max_strips = int(max_strips)
+        nb = int(L.pcmm_batched_workspace_bytes(ctypes.cast(self.probs, ctypes.c_void_p), n, self.max_strips))
+        if nb == 0:
+            raise ValueError("invalid batch")
+        self.ws = torch.empty(nb, dtype=torch.uint8, device=self.items[0][0].device)
+        self.info = BatchInfo()
+        _check(L.pcmm_batched_prepare(ctypes.cast(self.probs, ctypes.c_void_p), n, self.max_strips, _ptr(self.ws), nb,
+                                      ctypes.byref(self.info), _stream(stream)), "pcmm_batched_prepare")
+
+    def run(self, stream=None):
+        _check(lib().pcmm_batched_run(ctypes.byref(self.info), _ptr(self.ws), _stream(stream)),
+               "pcmm_batched_run")
+        return self.outs
 
 
 class Plan:

@@ -1,0 +1,105 @@
+"""The persistent batched launch: uneven instances (shapes, bit-widths,
+strip widths, several passes with alternating table buffers) give the same
+outputs as one pcmm_cussen call per instance and as the CPU oracle, on
+repeated runs and when replayed from a captured CUDA graph."""
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_2504_14497_gb300 import inputs, pcmm
+from tests.gpu_common import device, encrypt_gpu, mismatches
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+SPECS = [  # m, n, l, w, k
+    (37, 70, 20, 3, 1),     # 70 strips: several passes when max_strips is small
+    (64, 40, 45, 8, 1),
+    (9, 33, 5, 1, 6),
+    (50, 21, 33, 4, 2),
+    (1, 17, 3, 2, 0),
+    (70, 12, 1, 6, 2),
+    (16, 16, 16, 4, 3),
+]
+
+
+@pytest.fixture(scope="module")
+def dev():
+    return device()
+
+
+@pytest.fixture(scope="module")
+def batch_case(dev):
+    items, probs = [], []
+    for i, (m, n, l, w, k) in enumerate(SPECS):
+        pr = inputs.pcmm_problem(3100 + i, m, n, l, w)
+        ctB = encrypt_gpu(dev, pr)
+        A = torch.from_numpy(pr["A"]).to(dev)
+        items.append((A, ctB, l, w, k))
+        probs.append(pr)
+    return items, probs
+
+
+def _affine(jac, count):
+    out = pcmm.normalize(jac, count)
+    torch.cuda.synchronize()
+    return pcmm.planar_to_ct(pcmm.to_host_words(out), count)
+
+
+@pytest.mark.parametrize("max_strips", [0, 16, 7])
+def test_batched_equals_single_and_oracle(dev, batch_case, max_strips):
+    # 16 and 7 strips per pass: five and ten passes for the 70-strip instance,
+    # so table buffers are reused and gathers wait across passes.
+    items, probs = batch_case
+    b = pcmm.Batch(items, max_strips=max_strips)
+    outs = b.run()
+    torch.cuda.synchronize()
+    assert pcmm.workspace_status(b.ws) == 0
+    for (A, ctB, l, w, k), pr, out in zip(items, probs, outs):
+        m = A.shape[0]
+        single = _affine(pcmm.cussen(A, ctB, l, w, k=k), m * l)
+        got = _affine(out, m * l)
+        assert np.array_equal(got, single)
+        want = oracle.closed_form(pr["A"], pr["r"], pr["sk"], pr["B"]).reshape(-1, 2, 16)
+        assert mismatches(got, want) == 0
+    # A second run (queue and counters reset) gives the same bytes.
+    first = [o.clone() for o in outs]
+    b.run()
+    torch.cuda.synchronize()
+    assert pcmm.workspace_status(b.ws) == 0
+    for o, f, (A, _, l, _, _) in zip(b.outs, first, items):
+        assert np.array_equal(_affine(o, A.shape[0] * l), _affine(f, A.shape[0] * l))
+
+
+def test_batched_run_replays_from_a_cuda_graph(dev, batch_case):
+    items, _ = batch_case
+    b = pcmm.Batch(items)
+    b.run()
+    torch.cuda.synchronize()
+    ref = [_affine(o, A.shape[0] * l) for o, (A, _, l, _, _) in zip(b.outs, items)]
+    for o in b.outs:
+        o.fill_(0)
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            b.run()
+    torch.cuda.synchronize()
+    for rep in range(2):
+        g.replay()
+        torch.cuda.synchronize()
+        assert pcmm.workspace_status(b.ws) == 0
+        for o, r, (A, _, l, _, _) in zip(b.outs, ref, items):
+            assert np.array_equal(_affine(o, A.shape[0] * l), r), rep
+
+
+def test_autotuner_picks_a_valid_width_and_caches(dev, tmp_path):
+    from paper_2504_14497_gb300 import autotune
+
+    path = str(tmp_path / "tune.json")
+    k = autotune.tune(96, 64, 40, 4, device=dev, path=path)
+    assert k in autotune.candidates(96, 64, 40, 4)
+    cache = autotune.load_cache(path)
+    assert cache["96,64,40,4"]["k"] == k and len(cache["96,64,40,4"]["ms"]) >= 2
+    assert autotune.tune(96, 64, 40, 4, device=dev, path=path) == k   # served from the cache
