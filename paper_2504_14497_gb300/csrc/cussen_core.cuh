@@ -442,9 +442,12 @@ struct GatherArgs {
 // other SMs during the same launch.
 template <bool CG>
 __device__ __forceinline__ void gather_item(const GatherArgs& a, const PlanPtrs& P, long long gw) {
+    // Rows innermost: the warps resident at a time cover every row of a few
+    // column blocks, so each strip's table region is fetched once per block
+    // while those warps walk the strips together.
     const unsigned lane = threadIdx.x & 31u;
-    const int i = (int)(gw / (2 * a.njb));
-    const int rem = (int)(gw % (2 * a.njb));
+    const int i = (int)(gw % a.m);
+    const int rem = (int)(gw / a.m);
     const int c = rem / a.njb, jb = rem % a.njb;
     const int j = jb * 32 + (int)lane;
     const size_t ml = (size_t)a.m * a.l;
