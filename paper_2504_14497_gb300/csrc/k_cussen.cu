@@ -37,6 +37,17 @@
 using namespace pcmm;
 using namespace pcmm::cussen;
 
+// Minimum resident blocks per SM requested from the compiler (its register
+// budget).  Measured on GB300: 5 blocks for the gather (96 registers) and 4
+// for the table build (128) beat the uncapped allocations despite a few
+// spilled registers.  Build-time tunables.
+#ifndef PCMM_GATHER_MINBLOCKS
+#define PCMM_GATHER_MINBLOCKS 5
+#endif
+#ifndef PCMM_TABLE_MINBLOCKS
+#define PCMM_TABLE_MINBLOCKS 4
+#endif
+
 namespace {
 
 __global__ void __launch_bounds__(PLAN_THREADS) plan_kernel(const uint8_t* __restrict__ A, int m, int n,
@@ -44,14 +55,14 @@ __global__ void __launch_bounds__(PLAN_THREADS) plan_kernel(const uint8_t* __res
     plan_strip(A, m, n, w, k, emax, P, blockIdx.x);
 }
 
-__global__ void __launch_bounds__(128) table_kernel(TableArgs a, PlanPtrs P) {
+__global__ void __launch_bounds__(128, PCMM_TABLE_MINBLOCKS) table_kernel(TableArgs a, PlanPtrs P) {
     const long long item = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nitems = (long long)a.nstrips_chunk * 2 * a.njb;
     if (item >= nitems) return;
     table_item(a, P, item, a.scratch + (size_t)item * a.item_u4);
 }
 
-__global__ void __launch_bounds__(128) gather_kernel(GatherArgs a, PlanPtrs P) {
+__global__ void __launch_bounds__(128, PCMM_GATHER_MINBLOCKS) gather_kernel(GatherArgs a, PlanPtrs P) {
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (gw >= (long long)a.m * 2 * a.njb) return;
     gather_item<false>(a, P, gw);
