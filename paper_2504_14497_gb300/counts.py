@@ -15,13 +15,15 @@ needs none), each product costing two IMAD instructions (low and high word):
     doubling, a = -3  (dbl-2001-b, 3M + 5S)     372 products
     normalisation of one table entry (3M for simultaneous inversion,
       then 1S + 3M for x = X Z^-2, y = Y Z^-3)  420 products
+    affine addition inside a batch (3M for the shared inversion, then
+      1M + 1S + 1M for the slope, x3, y3)       356 products
 """
 from __future__ import annotations
 
 import numpy as np
 
 N_ITER = 4
-PRODUCTS = {"madd": 592, "add": 884, "dbl": 372, "norm": 420}
+PRODUCTS = {"madd": 592, "add": 884, "dbl": 372, "norm": 420, "affine": 356}
 IMAD_PER_PRODUCT = 2
 
 
@@ -42,15 +44,17 @@ def cussen_counts(A: np.ndarray, w: int, k: int, l: int, N: int = N_ITER) -> dic
 
     * ``table_dbl``/``table_ecsm_madd``: double-and-add of the level-N values;
     * ``table_add``: prefix sums of levels N-1..2 (Jacobian + Jacobian);
-    * ``table_madd``: level-1 prefix sums and k-tuple sums (Jacobian + affine);
+    * ``table_madd``: level-1 prefix sums (Jacobian + affine);
+    * ``table_affine``: k-tuple sums, affine additions sharing one inversion
+      per round;
     * ``table_norm``: entries normalised to affine (level 2, column tables when
-      k > 1, strip tables);
+      k > 1, strip tables when k = 1);
     * ``gather_madd``: accumulations of table entries into the outputs.
     Additions with an identity operand are copies and are not counted."""
     A = np.asarray(A).astype(np.int64) & ((1 << w) - 1)
     m, n = A.shape
     chains = 2 * l
-    tadd = tmadd = tdbl = tecsm = norm = 0
+    tadd = tmadd = tdbl = tecsm = norm = taff = 0
     nnz_rows = np.zeros(m, dtype=np.int64)
     for s0 in range(0, n, k):
         cols = A[:, s0:s0 + k]
@@ -72,18 +76,19 @@ def cussen_counts(A: np.ndarray, w: int, k: int, l: int, N: int = N_ITER) -> dic
         if kw > 1:
             for code in distinct:
                 parts = sum(1 for t in range(kw) if (int(code) >> (w * t)) & ((1 << w) - 1))
-                tmadd += chains * max(parts - 1, 0)
-        norm += chains * len(distinct)
+                taff += chains * max(parts - 1, 0)
+        else:
+            norm += chains * len(distinct)
         nnz_rows += codes != 0
     gather = chains * int(np.maximum(nnz_rows - 1, 0).sum())
     return {"gather_madd": gather, "table_add": tadd, "table_madd": tmadd, "table_dbl": tdbl,
-            "table_ecsm_madd": tecsm, "table_norm": norm}
+            "table_ecsm_madd": tecsm, "table_norm": norm, "table_affine": taff}
 
 
 def point_ops(c: dict) -> int:
     """Point additions and doublings of two finite points performed."""
     return (c["gather_madd"] + c["table_add"] + c["table_madd"] + c["table_dbl"]
-            + c["table_ecsm_madd"])
+            + c["table_ecsm_madd"] + c["table_affine"])
 
 
 def gather_imad(c: dict) -> int:
@@ -93,7 +98,8 @@ def gather_imad(c: dict) -> int:
 def table_imad(c: dict) -> int:
     p = (c["table_add"] * PRODUCTS["add"]
          + (c["table_madd"] + c["table_ecsm_madd"]) * PRODUCTS["madd"]
-         + c["table_dbl"] * PRODUCTS["dbl"] + c["table_norm"] * PRODUCTS["norm"])
+         + c["table_dbl"] * PRODUCTS["dbl"] + c["table_norm"] * PRODUCTS["norm"]
+         + c["table_affine"] * PRODUCTS["affine"])
     return p * IMAD_PER_PRODUCT
 
 

@@ -19,7 +19,7 @@ def test_counts_match_oracle_execution(w, k):
     assert c["gather_madd"] == oc["accum_add"]
     # Reconstruction and tuple additions: levels >= 2 as full additions,
     # level 1 and the tuples as mixed additions; same total as the oracle.
-    assert c["table_add"] + c["table_madd"] == oc["recon_add"]
+    assert c["table_add"] + c["table_madd"] + c["table_affine"] == oc["recon_add"]
     # Level-N multiplications: one per non-zero compressed value per chain.
     assert oc["ecsm"] == 2 * l * sum(len(counts._levels(pr["A"][:, j])[1]) for j in range(n))
 
