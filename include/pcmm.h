@@ -297,6 +297,13 @@ const char *pcmm_kernel_name(int id);
  *   P: Jacobian (6 quads) for ops 0-2, affine (4 quads) for op 3; Q: affine
  *   (op 1) or Jacobian (op 2); out: affine canonical (4 quads).
  * ---------------------------------------------------------------------- */
+/* pcmm_test_wait: runs the bounded device-side wait of the persistent batched
+ * kernel in `warps` warps (rounded up to a multiple of 4): each waits until
+ * *ctr >= target (ctr device int) for at most about a second, then gives up
+ * and ORs 4 (timeout) into *status (device); out[w] (device int per warp) is
+ * 1 if warp w saw the target, 0 if it gave up. */
+pcmm_status pcmm_test_wait(const int *ctr, int target, uint32_t *status, int *out, int warps,
+                           pcmm_stream_t stream);
 pcmm_status pcmm_test_field(int op, const uint32_t *a, const uint32_t *b, uint32_t *out,
                             size_t count, pcmm_stream_t stream);
 pcmm_status pcmm_test_point(int op, const uint32_t *P, const uint32_t *Q, const uint32_t *kscal,

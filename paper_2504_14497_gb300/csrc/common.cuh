@@ -14,7 +14,25 @@ namespace pcmm {
 enum : uint32_t {
     DEV_ERR_A_RANGE = 1u << 0,  // an entry of A is >= 2^w
     DEV_ERR_PLAN = 1u << 1,     // a plan size exceeded its bound
+    DEV_ERR_TIMEOUT = 1u << 2,  // a bounded device-side wait gave up
 };
+
+// Waits until *ctr >= target, polling with short sleeps, for at most about
+// 2^22 polls (roughly a second).  Gives up early when another warp has
+// already raised DEV_ERR_TIMEOUT in *status; raises it itself when the bound
+// runs out.  Returns whether the target was reached.  Call from one lane.
+__device__ __forceinline__ bool wait_at_least(const int* ctr, int target, uint32_t* status) {
+    for (int it = 0; it < (1 << 22); it++) {
+        if (*(volatile const int*)ctr >= target) {
+            __threadfence();
+            return true;
+        }
+        if (*(volatile const uint32_t*)status & DEV_ERR_TIMEOUT) return false;
+        __nanosleep(256);
+    }
+    atomicOr(status, DEV_ERR_TIMEOUT);
+    return false;
+}
 
 __device__ __forceinline__ fe fe_shfl_up(const fe& a, unsigned d) {
     fe r;

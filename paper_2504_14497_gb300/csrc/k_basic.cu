@@ -180,6 +180,15 @@ __global__ void __launch_bounds__(128) test_point_kernel(int op, const uint4* __
     if (valid) store_aff(out, count, i, o[0]);
 }
 
+// Every warp waits (bounded) for *ctr >= target; lane 0 records in out[warp]
+// whether the target was reached.
+__global__ void test_wait_kernel(const int* ctr, int target, uint32_t* status, int* out) {
+    if ((threadIdx.x & 31u) == 0) {
+        const bool ok = wait_at_least(ctr, target, status);
+        out[(blockIdx.x * blockDim.x + threadIdx.x) >> 5] = ok ? 1 : 0;
+    }
+}
+
 inline unsigned grid_for(size_t count, unsigned block) { return (unsigned)((count + block - 1) / block); }
 
 bool g_ready[64] = {false};
@@ -306,6 +315,14 @@ extern "C" pcmm_status pcmm_copy_columns(uint32_t* dst, size_t dst_ld, size_t ds
                           src_ld * 16, ncols * 16, nrows, cudaMemcpyDefault,
                           (cudaStream_t)stream) != cudaSuccess)
         return PCMM_ECUDA;
+    return PCMM_OK;
+}
+
+extern "C" pcmm_status pcmm_test_wait(const int* ctr, int target, uint32_t* status, int* out, int warps,
+                                      pcmm_stream_t stream) {
+    if (!ctr || !status || !out || warps < 1 || warps > 1024) return PCMM_EINVAL;
+    test_wait_kernel<<<(unsigned)((warps + 3) / 4), 128, 0, (cudaStream_t)stream>>>(ctr, target, status, out);
+    PCMM_CUDA_CHECK_LAUNCH();
     return PCMM_OK;
 }
 

@@ -34,7 +34,6 @@ using namespace pcmm::cussen;
 
 namespace {
 
-constexpr uint32_t DEV_ERR_TIMEOUT = 1u << 2;
 constexpr int TASK_TABLE = 0, TASK_GATHER = 1;
 constexpr int BATCH_THREADS = 128;
 
@@ -61,19 +60,6 @@ struct BatchHeader {            // device copy, first bytes of the workspace
     uint32_t status;
     int head;                   // next task index
 };
-
-__device__ __forceinline__ bool wait_at_least(const int* ctr, int target, uint32_t* status) {
-    for (int it = 0; it < (1 << 22); it++) {
-        if (*(volatile const int*)ctr >= target) {
-            __threadfence();
-            return true;
-        }
-        if (*(volatile const uint32_t*)status & DEV_ERR_TIMEOUT) return false;
-        __nanosleep(256);
-    }
-    atomicOr(status, DEV_ERR_TIMEOUT);
-    return false;
-}
 
 __global__ void __launch_bounds__(PLAN_THREADS) batched_plan_kernel(const Inst* __restrict__ insts,
                                                                     const int2* __restrict__ strip_map) {

@@ -27,9 +27,10 @@ EXPORTS = (
     "pcmm_version", "pcmm_status_string", "pcmm_init", "pcmm_keytable_bytes", "pcmm_keytable",
     "pcmm_encrypt", "pcmm_base_mul", "pcmm_schoolbook", "pcmm_cussen_choose_k", "pcmm_cussen_workspace_bytes",
     "pcmm_cussen", "pcmm_cussen_plan_bytes", "pcmm_cussen_plan", "pcmm_cussen_exec_bytes",
-    "pcmm_cussen_execute", "pcmm_batched_workspace_bytes", "pcmm_batched_prepare", "pcmm_batched_run",
+    "pcmm_cussen_execute", "pcmm_cussen_static", "pcmm_batched_workspace_bytes", "pcmm_batched_prepare", "pcmm_batched_run",
     "pcmm_workspace_status", "pcmm_copy_columns", "pcmm_normalize", "pcmm_profile_enable",
-    "pcmm_profile_read", "pcmm_kernel_count", "pcmm_kernel_name", "pcmm_test_field", "pcmm_test_point",
+    "pcmm_profile_read", "pcmm_kernel_count", "pcmm_kernel_name", "pcmm_test_wait", "pcmm_test_field",
+    "pcmm_test_point",
 )
 
 _lock = threading.Lock()
@@ -68,6 +69,7 @@ def lib():
                 "pcmm_cussen_plan": ([vp, ci, ci, ci, ci, vp, sz, vp], ci),
                 "pcmm_cussen_exec_bytes": ([ci, ci, ci, ci, ci], sz),
                 "pcmm_cussen_execute": ([vp, ci, ci, ci, ci, vp, ci, vp, vp, sz, vp], ci),
+                "pcmm_cussen_static": ([vp, ci, ci, ci, vp, ci, vp, ci, vp], ci),
                 "pcmm_workspace_status": ([vp, u32p, vp], ci),
                 "pcmm_copy_columns": ([vp, sz, sz, vp, sz, sz, sz, sz, vp], ci),
                 "pcmm_normalize": ([vp, sz, vp, vp], ci),
@@ -262,6 +264,19 @@ def cussen(A, ctB, l: int, w: int, k: int = 0, ws=None, out=None, stream=None):
     return out
 
 
+def cussen_static(A, ctB, l: int, w: int, k: int = 0, out=None, stream=None):
+    """Cussen PC-MM on the library's static device scratch (no allocation by
+    the library; ``out`` may be passed in so that none happens here either).
+    Raises PcmmError with PCMM_EUNSUPPORTED when the problem does not fit."""
+    torch = _torch()
+    m, n = A.shape
+    if out is None:
+        out = torch.empty(PCMM_JAC_WORDS * m * l, dtype=torch.int32, device=A.device)
+    _check(lib().pcmm_cussen_static(_ptr(A), m, n, w, _ptr(ctB), l, _ptr(out), k, _stream(stream)),
+           "pcmm_cussen_static")
+    return out
+
+
 class Problem(ctypes.Structure):
     _fields_ = [("A", ctypes.c_void_p), ("m", ctypes.c_int), ("n", ctypes.c_int), ("w", ctypes.c_int),
                 ("ctB", ctypes.c_void_p), ("l", ctypes.c_int), ("ctC", ctypes.c_void_p), ("k", ctypes.c_int)]
@@ -367,6 +382,15 @@ def normalize(ct_jac, count: int, out=None, stream=None):
 
 
 # ------------------------------------------------------------- unit tests
+
+def test_wait(ctr, target: int, status, out, warps: int, stream=None):
+    L = lib()
+    L.pcmm_test_wait.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_int, ctypes.c_void_p]
+    L.pcmm_test_wait.restype = ctypes.c_int
+    _check(L.pcmm_test_wait(_ptr(ctr), target, _ptr(status), _ptr(out), warps, _stream(stream)),
+           "pcmm_test_wait")
+
 
 def test_field(op: int, a, b=None, stream=None):
     torch = _torch()

@@ -103,3 +103,24 @@ def test_autotuner_picks_a_valid_width_and_caches(dev, tmp_path):
     cache = autotune.load_cache(path)
     assert cache["96,64,40,4"]["k"] == k and len(cache["96,64,40,4"]["ms"]) >= 2
     assert autotune.tune(96, 64, 40, 4, device=dev, path=path) == k   # served from the cache
+
+
+def test_bounded_wait_gives_up_and_reports(dev):
+    import time
+
+    ctr = torch.zeros(1, dtype=torch.int32, device=dev)       # nothing ever sets it
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    out = torch.full((8,), -1, dtype=torch.int32, device=dev)
+    t0 = time.perf_counter()
+    pcmm.test_wait(ctr, 1, status, out, 8)
+    torch.cuda.synchronize()
+    took = time.perf_counter() - t0
+    assert int(status.item()) & 4                      # timeout bit raised
+    assert (out == 0).all()                            # every warp gave up
+    assert took < 30
+    # The context is still usable, and a satisfied wait returns at once.
+    ctr.fill_(3)
+    status.zero_()
+    pcmm.test_wait(ctr, 2, status, out, 8)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0 and (out == 1).all()

@@ -79,3 +79,16 @@ def test_static_entry_rejects_problems_beyond_its_scratch(dev):
     assert "unsupported" in pcmm.status_string(rc)
     torch.cuda.synchronize()
     assert not dummy.any()      # nothing was launched
+
+
+def test_static_binding_matches_workspace_entry(dev):
+    m, n, l, w = 33, 20, 17, 4
+    A, ctB = _problem(dev, 777, m, n, l, w)
+    want = _affine(pcmm.cussen(A, ctB, l, w, k=2), m * l)
+    got = _affine(pcmm.cussen_static(A, ctB, l, w, k=2), m * l)
+    assert np.array_equal(got, want)
+    with pytest.raises(pcmm.PcmmError) as e:
+        pcmm.cussen_static(torch.zeros((1024, 1024), dtype=torch.uint8, device=dev),
+                           torch.zeros(64, dtype=torch.int32, device=dev), 4096, 8, k=1,
+                           out=torch.zeros(64, dtype=torch.int32, device=dev))
+    assert e.value.status == PCMM_EUNSUPPORTED
