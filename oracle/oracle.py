@@ -56,6 +56,7 @@ def _load():
             lib = ctypes.CDLL(_LIB)
             u32p = ctypes.POINTER(ctypes.c_uint32)
             u8p = ctypes.POINTER(ctypes.c_uint8)
+            u16p = ctypes.POINTER(ctypes.c_uint16)
             i64p = ctypes.POINTER(ctypes.c_int64)
             i32p = ctypes.POINTER(ctypes.c_int32)
             ll = ctypes.POINTER(ctypes.c_longlong)
@@ -75,9 +76,9 @@ def _load():
                 "orc_keygen": [u32p, u32p],
                 "orc_encrypt": [u32p, u8p, u32p, sz, u32p],
                 "orc_decrypt": [u32p, u32p, sz, ctypes.c_int64, i64p],
-                "orc_schoolbook": [u8p, ci, ci, ci, ci, u32p, u32p, ll],
-                "orc_cussen": [u8p, ci, ci, ci, ci, ci, ci, u32p, u32p, ll],
-                "orc_closed_form": [u8p, ci, ci, ci, u32p, u32p, u8p, i32p, sz, u32p],
+                "orc_schoolbook": [u16p, ci, ci, ci, ci, u32p, u32p, ll],
+                "orc_cussen": [u16p, ci, ci, ci, ci, ci, ci, u32p, u32p, ll],
+                "orc_closed_form": [u16p, ci, ci, ci, u32p, u32p, u8p, i32p, sz, u32p],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -244,8 +245,16 @@ def decrypt(sk, ct, mmax: int) -> np.ndarray:
 COUNT_KEYS = ("ecsm", "ecsm_dbl", "ecsm_add", "recon_add", "accum_add")
 
 
+def _plaintext(A) -> np.ndarray:
+    """A as contiguous uint16 (entries of up to 16 bits, the paper's t <= 16)."""
+    A = np.asarray(A)
+    if A.size and (int(A.min()) < 0 or int(A.max()) > 0xFFFF):
+        raise ValueError("entries of A must lie in [0, 2^16)")
+    return np.ascontiguousarray(A, dtype=np.uint16)
+
+
 def _pcmm_args(A, ctB):
-    A = np.ascontiguousarray(A, dtype=np.uint8)
+    A = _plaintext(A)
     ctB = _u32(ctB, (2, 16))
     m, n = A.shape
     if ctB.shape[0] != n:
@@ -258,7 +267,7 @@ def schoolbook(A, ctB, w: int):
     A, ctB, m, n, l = _pcmm_args(A, ctB)
     out = np.zeros((m, l, 2, 16), dtype=np.uint32)
     cnt = (ctypes.c_longlong * 5)()
-    _check(_load().orc_schoolbook(_p(A, ctypes.c_uint8), m, n, l, w, _p(ctB, ctypes.c_uint32),
+    _check(_load().orc_schoolbook(_p(A, ctypes.c_uint16), m, n, l, w, _p(ctB, ctypes.c_uint32),
                                   _p(out, ctypes.c_uint32), cnt), "schoolbook")
     return out, dict(zip(COUNT_KEYS, list(cnt)))
 
@@ -268,7 +277,7 @@ def cussen(A, ctB, w: int, k: int = 1, N: int = N_ITER):
     A, ctB, m, n, l = _pcmm_args(A, ctB)
     out = np.zeros((m, l, 2, 16), dtype=np.uint32)
     cnt = (ctypes.c_longlong * 5)()
-    _check(_load().orc_cussen(_p(A, ctypes.c_uint8), m, n, l, w, k, N, _p(ctB, ctypes.c_uint32),
+    _check(_load().orc_cussen(_p(A, ctypes.c_uint16), m, n, l, w, k, N, _p(ctB, ctypes.c_uint32),
                               _p(out, ctypes.c_uint32), cnt), "cussen")
     return out, dict(zip(COUNT_KEYS, list(cnt)))
 
@@ -278,7 +287,7 @@ def closed_form(A, r, sk, msg, pairs=None) -> np.ndarray:
 
     ``pairs``: int array [P, 2] of (i, j); default all m*l outputs, returned
     as uint32[m, l, 2, 16]; with pairs, uint32[P, 2, 16]."""
-    A = np.ascontiguousarray(A, dtype=np.uint8)
+    A = _plaintext(A)
     m, n = A.shape
     R = _u32(r, (8,))
     l = R.shape[1]
@@ -290,7 +299,7 @@ def closed_form(A, r, sk, msg, pairs=None) -> np.ndarray:
         pairs = np.stack([ii.ravel(), jj.ravel()], axis=1)
     pairs = np.ascontiguousarray(pairs, dtype=np.int32)
     out = np.zeros((pairs.shape[0], 2, 16), dtype=np.uint32)
-    _check(_load().orc_closed_form(_p(A, ctypes.c_uint8), m, n, l, _p(R, ctypes.c_uint32),
+    _check(_load().orc_closed_form(_p(A, ctypes.c_uint16), m, n, l, _p(R, ctypes.c_uint32),
                                    _p(S, ctypes.c_uint32), _p(msg, ctypes.c_uint8),
                                    _p(pairs, ctypes.c_int32), pairs.shape[0],
                                    _p(out, ctypes.c_uint32)), "closed_form")

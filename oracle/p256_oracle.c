@@ -643,10 +643,10 @@ static pt add_counted(const pt *a, const pt *b, long long *c) {
 /* Schoolbook PC-MM (Section 3.1): Enc(c_ij) = sum_k a_ik * Enc(b_kj), each
  * product by the ladder with t = w bits, accumulated by point additions.
  * w is the plaintext bit-width (entries of A must be < 2^w). */
-int orc_schoolbook(const uint8_t *A, int m, int n, int l, int w, const uint32_t *ctB,
+int orc_schoolbook(const uint16_t *A, int m, int n, int l, int w, const uint32_t *ctB,
                    uint32_t *ctC, long long *counts_out) {
     ensure_init();
-    if (m < 0 || n < 0 || l < 0 || w < 1 || w > 8) return -1;
+    if (m < 0 || n < 0 || l < 0 || w < 1 || w > 16) return -1;
     for (long long i = 0; i < (long long)m * n; i++) if (A[i] >> w) return -1;
     pt *B = (pt *)malloc(sizeof(pt) * 2 * (size_t)n * l + 1);
     pt *C = (pt *)malloc(sizeof(pt) * 2 * (size_t)m * l + 1);
@@ -773,10 +773,10 @@ static void cussen_apply(const cussen_plan *pl, const pt *P, int t, pt *out, pt 
  * reconstructed one by one as above, the distinct k-tuples of the strip
  * are formed by adding the per-column multiples, and every row adds the
  * entry of its tuple once.  Group results are identical for every k. */
-int orc_cussen(const uint8_t *A, int m, int n, int l, int w, int kstrip, int N,
+int orc_cussen(const uint16_t *A, int m, int n, int l, int w, int kstrip, int N,
                const uint32_t *ctB, uint32_t *ctC, long long *counts_out) {
     ensure_init();
-    if (m < 0 || n < 0 || l < 0 || w < 1 || w > 8 || kstrip < 1 || N < 1 || N > MAXLEV) return -1;
+    if (m < 0 || n < 0 || l < 0 || w < 1 || w > 16 || kstrip < 1 || N < 1 || N > MAXLEV) return -1;
     if (w * kstrip > 24) return -1;
     for (long long i = 0; i < (long long)m * n; i++) if (A[i] >> w) return -1;
     pt *B = (pt *)malloc(sizeof(pt) * 2 * (size_t)n * l + 1);
@@ -871,7 +871,7 @@ int orc_cussen(const uint8_t *A, int m, int n, int l, int w, int kstrip, int N,
  *   C2_ij = (sum_k a_ik (r_kj x + b_kj) mod q) G.
  * Computed for the npairs (i, j) listed in ij (2 ints each); out holds
  * npairs x 32 words.  r: n x l x 8 words; msg: n x l bytes. */
-int orc_closed_form(const uint8_t *A, int m, int n, int l, const uint32_t *r32,
+int orc_closed_form(const uint16_t *A, int m, int n, int l, const uint32_t *r32,
                     const uint32_t *sk32, const uint8_t *msg, const int32_t *ij, size_t npairs,
                     uint32_t *out) {
     ensure_pow2();

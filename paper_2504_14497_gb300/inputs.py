@@ -55,13 +55,15 @@ def uniform_scalars(rng: np.random.Generator, shape) -> np.ndarray:
 
 
 def pcmm_problem(seed: int, m: int, n: int, l: int, w: int, msg_bits: int = 8) -> dict:
-    """One PC-MM instance: plaintext A (m x n, w-bit), message matrix B
-    (n x l, msg_bits-bit), secret key sk and nonces r (n x l)."""
-    if not 1 <= w <= 8:
-        raise ValueError("w must be in [1, 8]")
+    """One PC-MM instance: plaintext A (m x n, w-bit; uint8 for w <= 8,
+    uint16 for 8 < w <= 16), message matrix B (n x l, msg_bits-bit), secret
+    key sk and nonces r (n x l)."""
+    if not 1 <= w <= 16:
+        raise ValueError("w must be in [1, 16]")
     s = streams(seed)
     sk = uniform_scalars(s["sk"], (1,))[0]
-    A = s["A"].integers(0, 1 << w, size=(m, n), dtype=np.uint8) if m * n else np.zeros((m, n), np.uint8)
+    adt = np.uint8 if w <= 8 else np.uint16
+    A = s["A"].integers(0, 1 << w, size=(m, n), dtype=adt) if m * n else np.zeros((m, n), adt)
     B = s["B"].integers(0, 1 << msg_bits, size=(n, l), dtype=np.uint8) if n * l else np.zeros((n, l), np.uint8)
     r = uniform_scalars(s["r"], (n, l))
     return {"sk": sk, "A": A, "B": B, "r": r, "m": m, "n": n, "l": l, "w": w}

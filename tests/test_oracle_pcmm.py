@@ -64,6 +64,39 @@ def test_bit_widths_and_ragged_strips(w):
     assert (sb == ref).all()
 
 
+@pytest.mark.parametrize("w", [9, 12, 16])
+def test_wide_values_agree_with_closed_form(w):
+    # The paper's t = 12 and 16 grid (Section 4): entries of A up to 16 bits.
+    pr, ct = _problem(80 + w, 14, 9, 3, w)
+    assert pr["A"].dtype == np.uint16 and int(pr["A"].max()) >= 1 << (w - 1)
+    ref = O.closed_form(pr["A"], pr["r"], pr["sk"], pr["B"])
+    cu, _ = O.cussen(pr["A"], ct, w, 1)
+    assert (cu == ref).all()
+    if 2 * w <= 24:
+        assert (O.cussen(pr["A"], ct, w, 2)[0] == ref).all()
+    sb, _ = O.schoolbook(pr["A"], ct, w)
+    assert (sb == ref).all()
+    AB = pr["A"].astype(np.int64) @ pr["B"].astype(np.int64)
+    assert (O.decrypt(pr["sk"], ref[:2], 9 * ((1 << w) - 1) * 255) == AB[:2]).all()
+
+
+def test_wide_values_duplicates_and_extremes():
+    # Columns mixing zeros, 1, 2^16 - 1 and repeated mid values, next to a
+    # column of distinct values: every compression level is exercised.
+    rng = np.random.default_rng(90)
+    m, n, l, w = 40, 6, 2, 16
+    A = rng.choice(np.array([0, 1, 2, 0x8000, 0xFFFE, 0xFFFF], dtype=np.uint16), size=(m, n))
+    A[:, 3] = np.arange(m, dtype=np.uint16) * 1637 + 3
+    pr = I.pcmm_problem(91, m, n, l, 8)
+    H = O.keygen(pr["sk"])
+    ct = O.encrypt(H, pr["B"], pr["r"])
+    ref = O.closed_form(A, pr["r"], pr["sk"], pr["B"])
+    assert (O.cussen(A, ct, w, 1)[0] == ref).all()
+    assert (O.schoolbook(A, ct, w)[0] == ref).all()
+    with pytest.raises(O.OracleError):
+        O.cussen(A, ct, 15, 1)          # 0xFFFF does not fit in 15 bits
+
+
 def test_degenerate_shapes_and_zero_matrix():
     pr, ct = _problem(61, 1, 1, 1, 4)
     ref = O.closed_form(pr["A"], pr["r"], pr["sk"], pr["B"])
