@@ -165,6 +165,13 @@ def recorded_traffic(kernel: str):
     return None
 
 
+def _host_plaintext(A):
+    """Host tensor of a plaintext matrix: uint8, or int16 holding the bits of
+    a uint16 matrix (entries of more than 8 bits)."""
+    import torch
+    return torch.from_numpy(A.view(np.int16) if A.dtype == np.uint16 else A)
+
+
 def make_problem(m, n, l, widths):
     from paper_2504_14497_gb300 import inputs
     pr = {w: inputs.pcmm_problem(SEED, m, n, l, w) for w in widths}
@@ -245,7 +252,7 @@ def run_ours(args, dist):
     runs = []
     for w in widths:
         k = pcmm.choose_k(m, n, l, w)
-        A = torch.from_numpy(problems[w]["A"]).to(dev)
+        A = _host_plaintext(problems[w]["A"]).to(dev)
         ws = pcmm.workspace(m, n, l, w, k, device=dev)
         jac = torch.empty(48 * m * l, dtype=torch.int32, device=dev)
         aff = torch.empty(32 * m * l, dtype=torch.int32, device=dev)
@@ -335,7 +342,7 @@ def run_ours(args, dist):
     # ---- end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
-        hA = [torch.from_numpy(problems[r["w"]]["A"]).pin_memory() for r in runs]
+        hA = [_host_plaintext(problems[r["w"]]["A"]).pin_memory() for r in runs]
         hB = pcmm.to_host_words(ctB).view(np.int32)
         hB = torch.from_numpy(hB.copy()).pin_memory()
         hC = [torch.empty(32 * m * l, dtype=torch.int32).pin_memory() for _ in runs]

@@ -63,8 +63,9 @@ typedef enum {
 
 #define PCMM_AFF_WORDS 32
 #define PCMM_JAC_WORDS 48
-#define PCMM_MAX_W 8      /* plaintext bit-width w of A: 1..8 */
-#define PCMM_MAX_WK 12    /* strip code width w * k is at most 12 bits */
+#define PCMM_MAX_W 8      /* bit-width w of a uint8 A: 1..8 */
+#define PCMM_MAX_W16 16   /* bit-width w of a uint16 A (the paper's t = 12, 16): 1..16 */
+#define PCMM_MAX_WK 16    /* strip code width w * k is at most 16 bits */
 #define PCMM_N_ITER 4     /* Cussen compression iterations N (Section 3.2) */
 
 /* Library ABI version (major * 10000 + minor * 100 + patch). */
@@ -126,14 +127,22 @@ pcmm_status pcmm_base_mul(const uint32_t *scalars, size_t count, uint32_t *point
 pcmm_status pcmm_schoolbook(const uint8_t *A, int m, int n, int w, const uint32_t *ctB, int l,
                             uint32_t *ctC, pcmm_stream_t stream);
 
+/* pcmm_schoolbook for plaintext entries of up to 16 bits: A is device uint16
+ * m x n (entries < 2^w), 1 <= w <= 16 (the paper's t = 12 and 16 grid,
+ * Section 4).  Otherwise as pcmm_schoolbook. */
+pcmm_status pcmm_schoolbook16(const uint16_t *A, int m, int n, int w, const uint32_t *ctB, int l,
+                              uint32_t *ctC, pcmm_stream_t stream);
+
 /* Strip width chosen by the built-in cost model for a problem shape: the k
- * in [1, 12/w] minimising the modelled point-addition work (table build,
- * normalisation and gather). */
+ * in [1, 16/w] minimising the modelled work (table build, normalisation and
+ * gather, the table work weighted by its lower measured issue efficiency).
+ * Accepts 1 <= w <= 16; returns 0 for invalid arguments. */
 int pcmm_cussen_choose_k(int m, int n, int l, int w);
 
-/* Workspace bytes pcmm_cussen needs for this shape and strip width k
- * (k = 0: the pcmm_cussen_choose_k value).  Returns 0 for invalid
- * arguments.  Larger workspaces let a call process more strips per pass. */
+/* Workspace bytes pcmm_cussen (w <= 8) or pcmm_cussen16 (w <= 16) needs for
+ * this shape and strip width k (k = 0: the pcmm_cussen_choose_k value).
+ * Returns 0 for invalid arguments.  Larger workspaces let a call process
+ * more strips per pass. */
 size_t pcmm_cussen_workspace_bytes(int m, int n, int l, int w, int k);
 
 /* Cussen PC-MM (Algorithms 2 and 3).  Strip width k = 1 is Algorithm 3 as
@@ -146,7 +155,7 @@ size_t pcmm_cussen_workspace_bytes(int m, int n, int l, int w, int k);
  * combines k adjacent columns into one table of the distinct k-tuples of
  * the strip, so the gather adds once per strip instead of once per column.
  * The result is identical for every k.
- * k: 1 <= k <= 12 / w, or 0 for pcmm_cussen_choose_k.
+ * k: 1 <= k <= 16 / w, or 0 for pcmm_cussen_choose_k.
  * ws: device workspace, 256-byte aligned, of at least
  * pcmm_cussen_workspace_bytes(m, n, l, w, k) bytes; its first 4 bytes are a
  * status word that kernels OR error bits into (1: an entry of A >= 2^w,
@@ -155,6 +164,15 @@ size_t pcmm_cussen_workspace_bytes(int m, int n, int l, int w, int k);
  * Errors: PCMM_EINVAL, PCMM_ENOMEM (workspace too small), PCMM_ECUDA. */
 pcmm_status pcmm_cussen(const uint8_t *A, int m, int n, int w, const uint32_t *ctB, int l,
                         uint32_t *ctC, int k, void *ws, size_t ws_bytes, pcmm_stream_t stream);
+
+/* pcmm_cussen for plaintext entries of up to 16 bits, the paper's wide
+ * values (t = 12 and 16, Sections 3.2 and 4): A is device uint16 m x n with
+ * entries < 2^w, 1 <= w <= 16, and 1 <= k <= 16 / w (so k = 1 for w > 8:
+ * each column is compressed by the N = 4 difference levels alone, with no
+ * table of all 2^w values).  Workspace, status word and errors as
+ * pcmm_cussen. */
+pcmm_status pcmm_cussen16(const uint16_t *A, int m, int n, int w, const uint32_t *ctB, int l,
+                          uint32_t *ctC, int k, void *ws, size_t ws_bytes, pcmm_stream_t stream);
 
 /* The same computation in two phases, so that the plan of a plaintext matrix
  * (it depends on A, w and k only: Algorithm 3 compresses each column of A

@@ -17,7 +17,7 @@ import numpy as np
 from . import pcmm
 
 def candidates(m: int, n: int, l: int, w: int) -> list:
-    kmax = max(1, min(12 // w, n))
+    kmax = max(1, min(pcmm.PCMM_MAX_WK // w, n))
     k0 = pcmm.choose_k(m, n, l, w)
     ks = {k for k in (k0 - 1, k0, k0 + 1, k0 + 2) if 1 <= k <= kmax}
     return sorted(ks)

@@ -18,7 +18,7 @@ constexpr int PLAN_THREADS = 256;
 
 struct Layout {
     int m, n, l, w, k;
-    int nstrips, n1max, l2max, emax, lp, njb;
+    int nstrips, n1max, l2max, emax, lp, njb, ptr_stride;
     size_t off_rank, off_nent, off_codes, off_len, off_vN, off_ptr, off_rank1, plan_bytes;
     size_t item_u4, items_per_strip, table_points_per_strip, per_strip_bytes;
 };
@@ -34,13 +34,19 @@ inline int level2_bound(int w) {
     return d < 1 ? 1 : d;
 }
 
+// Workspace layout of one PC-MM (host and device agree on it).  Entries of A
+// have up to PCMM_MAX_W16 bits; a strip code has w k <= PCMM_MAX_WK bits.
+// Per column the plan holds the level lengths, the level-N values (uint16,
+// l2max per column) and the tracking pointers of levels 1..N-1 (uint16:
+// n1max for level 1, then l2max per further level).
 inline bool make_layout(Layout& L, int m, int n, int l, int w, int k) {
-    if (m < 1 || n < 1 || l < 1 || w < 1 || w > PCMM_MAX_W || k < 1 || w * k > PCMM_MAX_WK) return false;
+    if (m < 1 || n < 1 || l < 1 || w < 1 || w > PCMM_MAX_W16 || k < 1 || w * k > PCMM_MAX_WK) return false;
     L.m = m; L.n = n; L.l = l; L.w = w; L.k = k;
     L.nstrips = (n + k - 1) / k;
     L.n1max = (1 << w) - 1 < m ? (1 << w) - 1 : m;
-    L.l2max = level2_bound(w);
+    L.l2max = level2_bound(w) < L.n1max ? level2_bound(w) : L.n1max;
     L.emax = (1 << (w * k)) - 1 < m ? (1 << (w * k)) - 1 : m;
+    L.ptr_stride = L.n1max + (NLEV > 2 ? NLEV - 2 : 0) * L.l2max;
     L.njb = (l + 31) / 32;
     L.lp = L.njb * 32;
     size_t off = 256;  // status word and padding
@@ -48,16 +54,17 @@ inline bool make_layout(Layout& L, int m, int n, int l, int w, int k) {
     L.off_nent = off;  off = align256(off + (size_t)L.nstrips * 4);
     L.off_codes = off; off = align256(off + (size_t)L.nstrips * L.emax * 2);
     L.off_len = off;   off = align256(off + (size_t)n * NLEV * 2);
-    L.off_vN = off;    off = align256(off + (size_t)n * 256);
-    L.off_ptr = off;   off = align256(off + (size_t)n * (NLEV > 1 ? NLEV - 1 : 1) * 256);
-    L.off_rank1 = off; off = align256(off + (size_t)n * 256);
+    L.off_vN = off;    off = align256(off + (size_t)n * L.l2max * 2);
+    L.off_ptr = off;   off = align256(off + (size_t)n * L.ptr_stride * 2);
+    L.off_rank1 = off; off = align256(off + (k > 1 ? (size_t)n * 256 : 0));
     L.plan_bytes = off;
-    // Per warp item (lane-planar): Jacobian column table and level ping-pong,
-    // affine level-2 entries, affine column tables and Jacobian tuples (k > 1),
-    // prefix products for the normalisations.
-    const size_t jac_ents = (size_t)L.n1max + 2 * (size_t)L.l2max + (k > 1 ? (size_t)L.emax : 0);
-    const size_t aff_ents = (size_t)L.l2max + (k > 1 ? (size_t)k * L.n1max : 0);
-    L.item_u4 = jac_ents * 6 * 32 + aff_ents * 4 * 32 + (size_t)L.emax * 2 * 32;
+    // Per warp item (lane-planar): Jacobian column table and level ping-pong;
+    // affine level-2 entries, affine column tables and tuple partial sums
+    // (k > 1); prefix products for the normalisations.
+    const size_t jac_ents = (size_t)L.n1max + 2 * (size_t)L.l2max;
+    const size_t aff_ents = (size_t)L.l2max + (k > 1 ? (size_t)k * L.n1max + (size_t)L.emax : 0);
+    const size_t pref_ents = (size_t)(L.emax > L.n1max ? L.emax : L.n1max);
+    L.item_u4 = jac_ents * 6 * 32 + aff_ents * 4 * 32 + pref_ents * 2 * 32;
     L.items_per_strip = 2 * (size_t)L.njb;
     L.table_points_per_strip = (size_t)L.emax * 2 * L.lp;
     L.per_strip_bytes = L.items_per_strip * L.item_u4 * 16 + align256(L.table_points_per_strip * 64);
@@ -70,9 +77,10 @@ struct PlanPtrs {
     int32_t* nent;
     uint16_t* codes;
     uint16_t* col_len;
-    uint8_t* col_vN;
-    uint8_t* col_ptr;
-    uint8_t* col_rank1;
+    uint16_t* col_vN;      // [col][l2max]
+    uint16_t* col_ptr;     // [col][ptr_stride]
+    uint8_t* col_rank1;    // [col][256] (k > 1, so w <= 8)
+    int n1max, l2max, ptr_stride, emax;
 };
 
 inline PlanPtrs plan_ptrs(const Layout& L, void* ws) {
@@ -83,10 +91,20 @@ inline PlanPtrs plan_ptrs(const Layout& L, void* ws) {
     P.nent = (int32_t*)(b + L.off_nent);
     P.codes = (uint16_t*)(b + L.off_codes);
     P.col_len = (uint16_t*)(b + L.off_len);
-    P.col_vN = b + L.off_vN;
-    P.col_ptr = b + L.off_ptr;
+    P.col_vN = (uint16_t*)(b + L.off_vN);
+    P.col_ptr = (uint16_t*)(b + L.off_ptr);
     P.col_rank1 = b + L.off_rank1;
+    P.n1max = L.n1max;
+    P.l2max = L.l2max;
+    P.ptr_stride = L.ptr_stride;
+    P.emax = L.emax;
     return P;
+}
+
+// Tracking pointers of level lev (1 .. NLEV-1) of column col: entry e of
+// level lev sits at position ptr[e] of level lev + 1.
+__device__ __forceinline__ uint16_t* col_level_ptr(const PlanPtrs& P, int col, int lev) {
+    return P.col_ptr + (size_t)col * P.ptr_stride + (lev == 1 ? 0 : P.n1max + (size_t)(lev - 2) * P.l2max);
 }
 
 __device__ __forceinline__ int warp_excl_scan(int v, int& total) {
@@ -120,42 +138,247 @@ __device__ __forceinline__ int extract_sorted(const uint32_t* bm, uint16_t* out,
     return total;
 }
 
-// Block-level plan of strip s (all PLAN_THREADS threads of the block call).
-__device__ __forceinline__ void plan_strip(const uint8_t* __restrict__ A, int m, int n, int w, int k,
-                                           int emax, const PlanPtrs& P, int s) {
-    __shared__ uint32_t spres[128];
-    __shared__ uint32_t spref[128];
-    __shared__ uint32_t wbm[PLAN_THREADS / 32][8];
-    __shared__ uint16_t wlev[PLAN_THREADS / 32][2][256];
-    __shared__ uint8_t wpos[PLAN_THREADS / 32][256];
+// ---- block-level helpers of the plan (blockDim.x == PLAN_THREADS) ----
+
+// Exclusive prefix sum of one value per thread over the block; every thread
+// receives the total.  All threads must call.
+__device__ __forceinline__ int block_excl_scan(int v, int& total) {
+    __shared__ int wsum[PLAN_THREADS / 32];
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    int wt;
+    const int x = warp_excl_scan(v, wt);
+    __syncthreads();
+    if (lane == 0) wsum[warp] = wt;
+    __syncthreads();
+    int base = 0, tot = 0;
+    for (int q = 0; q < PLAN_THREADS / 32; q++) {
+        const int t = wsum[q];
+        if (q < (int)warp) base += t;
+        tot += t;
+    }
+    total = tot;
+    return base + x;
+}
+
+// Exclusive prefix maximum (identity -1) of one value per thread.
+__device__ __forceinline__ int block_excl_max(int v) {
+    __shared__ int wmax[PLAN_THREADS / 32];
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int o = __shfl_up_sync(0xffffffffu, incl, d);
+        if ((int)lane >= d) incl = o > incl ? o : incl;
+    }
+    int ex = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (lane == 0) ex = -1;
+    __syncthreads();
+    if (lane == 31) wmax[warp] = incl;
+    __syncthreads();
+    for (int q = 0; q < (int)warp; q++) ex = wmax[q] > ex ? wmax[q] : ex;
+    return ex;
+}
+
+// Words [w0, w0 + wpt) of an nw-word presence map belong to this thread.
+__device__ __forceinline__ int map_words_per_thread(int nw) { return (nw + PLAN_THREADS - 1) / PLAN_THREADS; }
+
+// pf[x] = number of set bits in words 0..x-1 of bm; returns the total.
+__device__ __forceinline__ int map_prefix(const uint32_t* bm, uint32_t* pf, int nw) {
+    const int wpt = map_words_per_thread(nw);
+    const int w0 = (int)threadIdx.x * wpt;
+    int cnt = 0;
+    for (int q = 0; q < wpt; q++)
+        if (w0 + q < nw) cnt += __popc(bm[w0 + q]);
+    int total;
+    int base = block_excl_scan(cnt, total);
+    for (int q = 0; q < wpt; q++)
+        if (w0 + q < nw) {
+            pf[w0 + q] = (uint32_t)base;
+            base += __popc(bm[w0 + q]);
+        }
+    __syncthreads();
+    return total;
+}
+
+// Position of the present value v in the sorted list of present values.
+__device__ __forceinline__ int map_rank(const uint32_t* bm, const uint32_t* pf, uint32_t v) {
+    return (int)(pf[v >> 5] + __popc(bm[v >> 5] & ((1u << (v & 31u)) - 1u)));
+}
+
+__device__ __forceinline__ void map_clear(uint32_t* bm, int nw) {
+    for (int x = threadIdx.x; x < nw; x += PLAN_THREADS) bm[x] = 0u;
+}
+
+// Levels 2..N of one column whose values have up to 16 bits (w > 8, hence
+// k = 1), computed by the whole block.  Level 1 (the sorted distinct
+// non-zero values) is given as the presence map bm1 of nw words with its
+// prefix counts pf1.  Level q + 1 is the sorted distinct set of the
+// differences of consecutive level-q values (the first minus zero); the
+// tracking pointer of a level-q entry is the position of its difference in
+// level q + 1.  bm/pf: nw-word work maps; lvA/lvB: lists of l2max entries.
+__device__ __forceinline__ void plan_column_wide(const uint32_t* bm1, const uint32_t* pf1, int nw, int len1,
+                                                 int col, const PlanPtrs& P, uint32_t* bm, uint32_t* pf,
+                                                 uint16_t* lvA, uint16_t* lvB) {
+    const int wpt = map_words_per_thread(nw);
+    const int w0 = (int)threadIdx.x * wpt;
+    if (threadIdx.x == 0) P.col_len[(size_t)col * NLEV] = (uint16_t)len1;
+    // Level 1 -> 2.  The predecessor of the first value in this thread's
+    // words is the largest value in the words before them.
+    int last = -1;
+    for (int q = 0; q < wpt; q++)
+        if (w0 + q < nw && bm1[w0 + q]) last = (w0 + q) * 32 + 31 - __clz(bm1[w0 + q]);
+    const int prev0 = block_excl_max(last);
+    map_clear(bm, nw);
+    __syncthreads();
+    for (int pass = 0; pass < 2; pass++) {
+        int prev = prev0 < 0 ? 0 : prev0;
+        uint16_t* ptr1 = col_level_ptr(P, col, 1);
+        for (int q = 0; q < wpt; q++) {
+            if (w0 + q >= nw) break;
+            uint32_t x = bm1[w0 + q];
+            while (x) {
+                const uint32_t v = (uint32_t)(w0 + q) * 32u + (uint32_t)(__ffs(x) - 1);
+                const uint32_t d = v - (uint32_t)prev;
+                if (pass == 0) atomicOr(&bm[d >> 5], 1u << (d & 31u));
+                else ptr1[map_rank(bm1, pf1, v)] = (uint16_t)map_rank(bm, pf, d);
+                prev = (int)v;
+                x &= x - 1u;
+            }
+        }
+        __syncthreads();
+        if (pass == 0) map_prefix(bm, pf, nw);
+    }
+    uint16_t* cur = lvA;
+    uint16_t* nxt = lvB;
+    int len = 0;
+    for (int lev = 1; lev < NLEV; lev++) {
+        if (lev > 1) {
+            // Differences of the level-lev list into the work map.
+            map_clear(bm, nw);
+            __syncthreads();
+            for (int e = threadIdx.x; e < len; e += PLAN_THREADS) {
+                const uint32_t d = (uint32_t)cur[e] - (e ? (uint32_t)cur[e - 1] : 0u);
+                atomicOr(&bm[d >> 5], 1u << (d & 31u));
+            }
+            __syncthreads();
+            map_prefix(bm, pf, nw);
+            uint16_t* ptr = col_level_ptr(P, col, lev);
+            for (int e = threadIdx.x; e < len; e += PLAN_THREADS) {
+                const uint32_t d = (uint32_t)cur[e] - (e ? (uint32_t)cur[e - 1] : 0u);
+                ptr[e] = (uint16_t)map_rank(bm, pf, d);
+            }
+        }
+        // Level lev + 1: the sorted present values of the work map.
+        int nlen;
+        {
+            int cnt = 0;
+            for (int q = 0; q < wpt; q++)
+                if (w0 + q < nw) cnt += __popc(bm[w0 + q]);
+            block_excl_scan(cnt, nlen);
+        }
+        for (int q = 0; q < wpt; q++) {
+            if (w0 + q >= nw) break;
+            uint32_t x = bm[w0 + q];
+            while (x) {
+                const uint32_t d = (uint32_t)(w0 + q) * 32u + (uint32_t)(__ffs(x) - 1);
+                const int r = map_rank(bm, pf, d);
+                if (r < P.l2max) nxt[r] = (uint16_t)d;
+                x &= x - 1u;
+            }
+        }
+        if (threadIdx.x == 0) P.col_len[(size_t)col * NLEV + lev] = (uint16_t)nlen;
+        __syncthreads();
+        uint16_t* tmp = cur; cur = nxt; nxt = tmp;
+        len = nlen < P.l2max ? nlen : P.l2max;
+    }
+    for (int e = threadIdx.x; e < len; e += PLAN_THREADS) P.col_vN[(size_t)col * P.l2max + e] = cur[e];
+    __syncthreads();
+}
+
+// Block-level plan of strip s (all PLAN_THREADS threads of the block call):
+// the presence map of the strip's codes (a code is the k-tuple of a row's
+// entries, w bits each), each row's rank among the distinct non-zero codes,
+// the list of distinct codes (k > 1) and the compression levels of every
+// column of the strip.  TA is the element type of A (uint8 or uint16).
+template <class TA>
+__device__ __forceinline__ void plan_strip(const TA* __restrict__ A, int m, int n, int w, int k,
+                                           const PlanPtrs& P, int s) {
+    constexpr int MAP_WORDS = 1 << (PCMM_MAX_WK - 5);
+    __shared__ uint32_t spres[MAP_WORDS];
+    __shared__ uint32_t spref[MAP_WORDS];
+    __shared__ uint32_t work[2 * MAP_WORDS];
+    __shared__ uint16_t lv[2][512];
     const int c0 = s * k;
     const int kw = (c0 + k <= n) ? k : n - c0;
     const uint32_t amask = (1u << w) - 1u;
     const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const int emax = P.emax;
 
-    // ---- per-column compression levels (one warp per column) ----
+    // ---- strip codes, distinct codes and per-row ranks ----
+    const int cbits = w * k;
+    const int nwc = cbits > 5 ? 1 << (cbits - 5) : 1;
+    map_clear(spres, nwc);
+    __syncthreads();
+    bool bad = false;
+    for (int i = threadIdx.x; i < m; i += PLAN_THREADS) {
+        uint32_t code = 0;
+        for (int t = 0; t < kw; t++) {
+            const uint32_t v = (uint32_t)A[(size_t)i * n + c0 + t];
+            bad |= v > amask;
+            code |= (v & amask) << (w * t);
+        }
+        if (code) atomicOr(&spres[code >> 5], 1u << (code & 31u));
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(P.status, DEV_ERR_A_RANGE);
+    const int total = map_prefix(spres, spref, nwc);
+    if (threadIdx.x == 0) P.nent[s] = total;
+    for (int i = threadIdx.x; i < m; i += PLAN_THREADS) {
+        uint32_t code = 0;
+        for (int t = 0; t < kw; t++) code |= ((uint32_t)A[(size_t)i * n + c0 + t] & amask) << (w * t);
+        P.rank[(size_t)s * m + i] = code ? (uint16_t)map_rank(spres, spref, code) : NO_RANK;
+    }
+    if (k > 1) {
+        for (int wd = threadIdx.x; wd < nwc; wd += PLAN_THREADS) {
+            uint32_t bits = spres[wd];
+            uint32_t r = spref[wd];
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                if ((int)r < emax) P.codes[(size_t)s * emax + r] = (uint16_t)(wd * 32 + b);
+                r++;
+                bits &= bits - 1u;
+            }
+        }
+    }
+
+    if (w > 8) {
+        // ---- wide values: k = 1, the strip map is the column's level 1 ----
+        plan_column_wide(spres, spref, 1 << (w - 5), total, c0, P, work, work + MAP_WORDS, lv[0], lv[1]);
+        return;
+    }
+
+    // ---- narrow values: per-column levels, one warp per column ----
+    uint32_t* wbm = work + warp * 8;                                                   // 8 words
+    uint16_t* wlev = (uint16_t*)(work + 64) + (size_t)warp * 512;                      // 2 x 256
+    uint8_t* pos = (uint8_t*)(work + 64 + 256 * (PLAN_THREADS / 32)) + (size_t)warp * 256;
     for (int t = (int)warp; t < kw; t += PLAN_THREADS / 32) {
         const int col = c0 + t;
-        uint32_t* bm = wbm[warp];
-        uint8_t* pos = wpos[warp];
+        uint32_t* bm = wbm;
         if (lane < 8) bm[lane] = 0u;
         __syncwarp();
-        bool bad = false;
         for (int i = (int)lane; i < m; i += 32) {
-            uint32_t v = A[(size_t)i * n + col];
-            bad |= v > amask;
-            v &= amask;
+            const uint32_t v = (uint32_t)A[(size_t)i * n + col] & amask;
             if (v) atomicOr(&bm[v >> 5], 1u << (v & 31u));
         }
-        if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(P.status, DEV_ERR_A_RANGE);
         __syncwarp();
-        uint16_t* cur = wlev[warp][0];
-        uint16_t* nxt = wlev[warp][1];
+        uint16_t* cur = wlev;
+        uint16_t* nxt = wlev + 256;
         int len = extract_sorted(bm, cur, pos);
-        // value -> level-1 position, for the k-tuple assembly
-        for (int v = (int)lane; v < 256; v += 32) {
-            const bool present = v > 0 && ((bm[v >> 5] >> (v & 31)) & 1u);
-            P.col_rank1[(size_t)col * 256 + v] = present ? pos[v] : (uint8_t)0xff;
+        if (k > 1) {
+            // value -> level-1 position, for the k-tuple assembly
+            for (int v = (int)lane; v < 256; v += 32) {
+                const bool present = v > 0 && ((bm[v >> 5] >> (v & 31)) & 1u);
+                P.col_rank1[(size_t)col * 256 + v] = present ? pos[v] : (uint8_t)0xff;
+            }
         }
         if (lane == 0) P.col_len[(size_t)col * NLEV] = (uint16_t)len;
         __syncwarp();
@@ -170,64 +393,23 @@ __device__ __forceinline__ void plan_strip(const uint8_t* __restrict__ A, int m,
             }
             __syncwarp();
             const int nlen = extract_sorted(bm, nxt, pos);
+            uint16_t* ptr = col_level_ptr(P, col, lev);
             for (int e = (int)lane; e < len; e += 32) {
                 const int d = (int)cur[e] - (e ? (int)cur[e - 1] : 0);
-                P.col_ptr[((size_t)col * (NLEV - 1) + (lev - 1)) * 256 + e] = pos[d];
+                ptr[e] = pos[d];
             }
             if (lane == 0) P.col_len[(size_t)col * NLEV + lev] = (uint16_t)nlen;
             __syncwarp();
             uint16_t* tmp = cur; cur = nxt; nxt = tmp;
-            len = nlen;
+            len = nlen < P.l2max ? nlen : P.l2max;
         }
-        for (int e = (int)lane; e < len; e += 32) P.col_vN[(size_t)col * 256 + e] = (uint8_t)cur[e];
+        for (int e = (int)lane; e < len; e += 32) P.col_vN[(size_t)col * P.l2max + e] = cur[e];
         __syncwarp();
-    }
-
-    // ---- strip codes, distinct codes and per-row ranks (whole block) ----
-    for (int x = threadIdx.x; x < 128; x += blockDim.x) spres[x] = 0u;
-    __syncthreads();
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        uint32_t code = 0;
-        for (int t = 0; t < kw; t++) code |= ((uint32_t)A[(size_t)i * n + c0 + t] & amask) << (w * t);
-        if (code) atomicOr(&spres[code >> 5], 1u << (code & 31u));
-    }
-    __syncthreads();
-    if (warp == 0) {
-        int cnt = 0;
-        for (int q = 0; q < 4; q++) cnt += __popc(spres[lane * 4 + q]);
-        int total;
-        int base = warp_excl_scan(cnt, total);
-        for (int q = 0; q < 4; q++) {
-            spref[lane * 4 + q] = (uint32_t)base;
-            base += __popc(spres[lane * 4 + q]);
-        }
-        if (lane == 0) P.nent[s] = total;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        uint32_t code = 0;
-        for (int t = 0; t < kw; t++) code |= ((uint32_t)A[(size_t)i * n + c0 + t] & amask) << (w * t);
-        uint16_t r = NO_RANK;
-        if (code) r = (uint16_t)(spref[code >> 5] + __popc(spres[code >> 5] & ((1u << (code & 31u)) - 1u)));
-        P.rank[(size_t)s * m + i] = r;
-    }
-    if (k > 1) {
-        for (int wd = threadIdx.x; wd < 128; wd += blockDim.x) {
-            uint32_t bits = spres[wd];
-            uint32_t r = spref[wd];
-            while (bits) {
-                const int b = __ffs(bits) - 1;
-                if ((int)r < emax) P.codes[(size_t)s * emax + r] = (uint16_t)(wd * 32 + b);
-                r++;
-                bits &= bits - 1u;
-            }
-        }
     }
 }
 
 struct TableArgs {
     const uint4* ctB;      // affine ciphertext matrix n x l
-    const uint8_t* A;
     int m, n, l, w, k, lp, njb, n1max, l2max, emax;
     int s0, nstrips_chunk;
     uint4* scratch;        // lane-planar per-item scratch
@@ -338,10 +520,10 @@ __device__ __forceinline__ void table_item(const TableArgs& a, const PlanPtrs& P
     uint4* coltab = scratch;                                              // n1max Jacobian
     uint4* levA = coltab + (size_t)a.n1max * 192;                         // l2max Jacobian
     uint4* levB = levA + (size_t)a.l2max * 192;                           // l2max Jacobian
-    uint4* ents_x = levB + (size_t)a.l2max * 192;                         // emax Jacobian (k > 1)
-    uint4* l2aff = ents_x + (a.k > 1 ? (size_t)a.emax * 192 : 0);         // l2max affine
+    uint4* l2aff = levB + (size_t)a.l2max * 192;                          // l2max affine
     uint4* colaff = l2aff + (size_t)a.l2max * 128;                        // k * n1max affine (k > 1)
-    uint4* pref = colaff + (a.k > 1 ? (size_t)a.k * a.n1max * 128 : 0);   // emax field elements
+    uint4* part = colaff + (a.k > 1 ? (size_t)a.k * a.n1max * 128 : 0);   // emax affine (k > 1)
+    uint4* pref = part + (a.k > 1 ? (size_t)a.emax * 128 : 0);            // max(emax, n1max) field elements
 
     const int E = P.nent[s];
     const size_t tbase = (size_t)s_local * a.emax;
@@ -365,13 +547,13 @@ __device__ __forceinline__ void table_item(const TableArgs& a, const PlanPtrs& P
         uint4* src = levA;
         for (int e = 0; e < lens[NLEV - 1]; e++) {
             jac T;
-            jac_mul_small(T, Pb, P.col_vN[(size_t)col * 256 + e]);
+            jac_mul_small(T, Pb, P.col_vN[(size_t)col * P.l2max + e]);
             lp_store_jac(src, e, lane, T);
         }
         uint4* alt = levB;
         // Levels N-1..2: un-sort by the tracking pointers, then prefix sums.
         for (int lev = NLEV - 1; lev >= 2; lev--) {
-            const uint8_t* ptr = P.col_ptr + ((size_t)col * (NLEV - 1) + (lev - 1)) * 256;
+            const uint16_t* ptr = col_level_ptr(P, col, lev);
             jac acc, D;
             jac_set_inf(acc);
             for (int e = 0; e < lens[lev - 1]; e++) {
@@ -386,7 +568,7 @@ __device__ __forceinline__ void table_item(const TableArgs& a, const PlanPtrs& P
         lp_normalize(src, lens[1], pref, lane, [&](int e, const aff& q) { lp_store_aff(l2aff, e, lane, q); });
         // Level 1: the multiples of the column's sorted distinct values.
         {
-            const uint8_t* ptr = P.col_ptr + (size_t)col * (NLEV - 1) * 256;
+            const uint16_t* ptr = col_level_ptr(P, col, 1);
             jac acc;
             aff D;
             jac_set_inf(acc);
@@ -417,7 +599,6 @@ __device__ __forceinline__ void table_item(const TableArgs& a, const PlanPtrs& P
     // instead of a mixed addition and a normalisation.  Pairs the affine
     // formula cannot take (infinity, equal or opposite points) use the
     // complete Jacobian addition and their own inversion on a rare branch.
-    uint4* part = ents_x;   // affine partial sums (4 quads per entry)
     auto comp = [&](uint32_t code, int nth, uint32_t& v) -> int {
         int cnt = 0;
         for (int t = 0; t < kw; t++) {
@@ -578,19 +759,30 @@ inline double expected_distinct_nonzero(int m, int bits) {
     return d < 0 ? 0 : d;
 }
 
-// Modelled work in field multiplications (a squaring counted as one).
+// Modelled time of one PC-MM in field-multiplication units (a squaring
+// counted as one) for strip width k.  Gather: one mixed addition (11) per
+// row, strip and ciphertext chain with a non-zero code.  Table build: per
+// column the level-1 prefix sums (mixed additions) and the level-N
+// double-and-add (about 2w operations of 8); the normalisation (7 per entry)
+// of the strip table (k = 1) or of the column tables (k > 1); for k > 1 the
+// tuple entries by affine additions (6 per further non-zero component).  The
+// table work is weighted by 1.9, fitted to GB300 timings of the
+// 1024 x 1024 x 256 product for every w and k (the table build issues its
+// multiplications less efficiently than the gather, and its tuple rounds
+// reload their operands from scratch).
 inline double model_cost(int m, int n, int l, int w, int k) {
-    const double MADD = 11, ADD = 16, DBL = 8, NORM = 7;
+    const double MADD = 11, DBL = 8, NORM = 7, AFF = 6, TABLE_WEIGHT = 1.9;
     const double chains = 2.0 * l;
     const int nstrips = (n + k - 1) / k;
     const double n1 = expected_distinct_nonzero(m, w);
     const double E = k == 1 ? n1 : expected_distinct_nonzero(m, w * k);
-    double col = n * chains * (n1 * ADD + 2.0 * w * DBL);
-    double tup = k > 1 ? nstrips * chains * E * (k - 1) * ADD : 0.0;
-    double norm = nstrips * chains * E * NORM;
-    double nz = 1.0 - ldexp(1.0, -w * k);
-    double gather = (double)m * chains * nstrips * nz * MADD;
-    return col + tup + norm + gather;
+    const double nz1 = 1.0 - ldexp(1.0, -w);
+    const double col = n * chains * (n1 * MADD + 2.0 * w * DBL);
+    const double norm = (k == 1 ? nstrips * E : n * n1) * chains * NORM;
+    const double extra = k * nz1 - 1.0;
+    const double tup = k > 1 ? nstrips * chains * E * (extra > 0 ? extra : 0.0) * AFF : 0.0;
+    const double gather = (double)m * chains * nstrips * (1.0 - ldexp(1.0, -w * k)) * MADD;
+    return gather + TABLE_WEIGHT * (col + norm + tup);
 }
 
 

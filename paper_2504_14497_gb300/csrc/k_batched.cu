@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(PLAN_THREADS) batched_plan_kernel(const Inst* 
                                                                     const int2* __restrict__ strip_map) {
     const int2 is = strip_map[blockIdx.x];
     const Inst& I = insts[is.x];
-    plan_strip(I.A, I.m, I.n, I.w, I.k, I.emax, I.P, is.y);
+    plan_strip(I.A, I.m, I.n, I.w, I.k, I.P, is.y);
 }
 
 __global__ void __launch_bounds__(BATCH_THREADS) batched_kernel(const Inst* __restrict__ insts,
@@ -102,7 +102,6 @@ __global__ void __launch_bounds__(BATCH_THREADS) batched_kernel(const Inst* __re
             if (!__shfl_sync(0xffffffffu, ok, 0)) break;
             TableArgs ta;
             ta.ctB = I.ctB;
-            ta.A = nullptr;
             ta.m = I.m; ta.n = I.n; ta.l = I.l; ta.w = I.w; ta.k = I.k;
             ta.lp = I.lp; ta.njb = I.njb; ta.n1max = I.n1max; ta.l2max = I.l2max; ta.emax = I.emax;
             ta.s0 = s0; ta.nstrips_chunk = sc;
@@ -166,7 +165,7 @@ pcmm_status build_layout(const pcmm_problem* probs, int count, int max_strips, i
     size_t off = 256;
     for (int i = 0; i < count; i++) {
         const pcmm_problem& p = probs[i];
-        if (!p.A || !p.ctB || !p.ctC) return PCMM_EINVAL;
+        if (!p.A || !p.ctB || !p.ctC || p.w > PCMM_MAX_W) return PCMM_EINVAL;
         int k = p.k ? p.k : pcmm_cussen_choose_k(p.m, p.n, p.l, p.w);
         if (!make_layout(Ls[i], p.m, p.n, p.l, p.w, k)) return PCMM_EINVAL;
     }
@@ -291,8 +290,8 @@ extern "C" pcmm_status pcmm_batched_prepare(const pcmm_problem* probs, int count
         P.nent = (int32_t*)(b + (uintptr_t)P.nent);
         P.codes = (uint16_t*)(b + (uintptr_t)P.codes);
         P.col_len = (uint16_t*)(b + (uintptr_t)P.col_len);
-        P.col_vN = (uint8_t*)(b + (uintptr_t)P.col_vN);
-        P.col_ptr = (uint8_t*)(b + (uintptr_t)P.col_ptr);
+        P.col_vN = (uint16_t*)(b + (uintptr_t)P.col_vN);
+        P.col_ptr = (uint16_t*)(b + (uintptr_t)P.col_ptr);
         P.col_rank1 = (uint8_t*)(b + (uintptr_t)P.col_rank1);
         P.status = (uint32_t*)base;        // all instances report into the batch status word
     }

@@ -50,9 +50,10 @@ using namespace pcmm::cussen;
 
 namespace {
 
-__global__ void __launch_bounds__(PLAN_THREADS) plan_kernel(const uint8_t* __restrict__ A, int m, int n,
-                                                            int w, int k, int emax, PlanPtrs P) {
-    plan_strip(A, m, n, w, k, emax, P, blockIdx.x);
+template <class TA>
+__global__ void __launch_bounds__(PLAN_THREADS) plan_kernel(const TA* __restrict__ A, int m, int n, int w,
+                                                            int k, PlanPtrs P) {
+    plan_strip(A, m, n, w, k, P, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(128, PCMM_TABLE_MINBLOCKS) table_kernel(TableArgs a, PlanPtrs P) {
@@ -71,17 +72,21 @@ __global__ void __launch_bounds__(128, PCMM_GATHER_MINBLOCKS) gather_kernel(Gath
 }  // namespace
 
 extern "C" int pcmm_cussen_choose_k(int m, int n, int l, int w) {
-    if (m < 1 || n < 1 || l < 1 || w < 1 || w > PCMM_MAX_W) return 0;
+    if (m < 1 || n < 1 || l < 1 || w < 1 || w > PCMM_MAX_W16) return 0;
+    // A wider strip must win by 3%: its tables and scratch grow with 2^(w k).
     int best = 1;
     double bc = model_cost(m, n, l, w, 1);
     for (int k = 2; w * k <= PCMM_MAX_WK && k <= n; k++) {
         double c = model_cost(m, n, l, w, k);
-        if (c < bc) { bc = c; best = k; }
+        if (c < 0.97 * bc) { bc = c; best = k; }
     }
     return best;
 }
 
-static const size_t TARGET_ITEMS = 4096;
+#ifndef PCMM_TARGET_ITEMS
+#define PCMM_TARGET_ITEMS 4096
+#endif
+static const size_t TARGET_ITEMS = PCMM_TARGET_ITEMS;
 
 extern "C" size_t pcmm_cussen_workspace_bytes(int m, int n, int l, int w, int k) {
     if (k == 0) k = pcmm_cussen_choose_k(m, n, l, w);
@@ -99,11 +104,12 @@ size_t default_strips(const Layout& L);
 
 namespace {
 
-pcmm_status launch_plan(const Layout& L, const uint8_t* A, const PlanPtrs& P, cudaStream_t st) {
+template <class TA>
+pcmm_status launch_plan(const Layout& L, const TA* A, const PlanPtrs& P, cudaStream_t st) {
     if (cudaMemsetAsync(P.status, 0, 4, st) != cudaSuccess) return PCMM_ECUDA;
     {
         ProfScope ps(KID_PLAN, st);
-        plan_kernel<<<L.nstrips, PLAN_THREADS, 0, st>>>(A, L.m, L.n, L.w, L.k, L.emax, P);
+        plan_kernel<TA><<<L.nstrips, PLAN_THREADS, 0, st>>>(A, L.m, L.n, L.w, L.k, P);
     }
     PCMM_CUDA_CHECK_LAUNCH();
     return PCMM_OK;
@@ -119,7 +125,6 @@ pcmm_status launch_exec(const Layout& L, const PlanPtrs& P, const uint32_t* ctB,
         const int sc = (int)((size_t)(L.nstrips - s0) < S ? (size_t)(L.nstrips - s0) : S);
         TableArgs ta;
         ta.ctB = (const uint4*)ctB;
-        ta.A = nullptr;
         ta.m = L.m; ta.n = L.n; ta.l = L.l; ta.w = L.w; ta.k = L.k;
         ta.lp = L.lp; ta.njb = L.njb; ta.n1max = L.n1max; ta.l2max = L.l2max; ta.emax = L.emax;
         ta.s0 = s0; ta.nstrips_chunk = sc;
@@ -158,11 +163,13 @@ size_t default_strips(const Layout& L) {
 
 }  // namespace
 
-extern "C" pcmm_status pcmm_cussen(const uint8_t* A, int m, int n, int w, const uint32_t* ctB, int l,
-                                   uint32_t* ctC, int k, void* ws, size_t ws_bytes,
-                                   pcmm_stream_t stream) {
+namespace {
+
+template <class TA>
+pcmm_status cussen_call(const TA* A, int m, int n, int w, const uint32_t* ctB, int l, uint32_t* ctC, int k,
+                        void* ws, size_t ws_bytes, pcmm_stream_t stream) {
     if (!A || !ctB || !ctC || !ws || ((uintptr_t)ws & 255u)) return PCMM_EINVAL;
-    if (m < 1 || n < 1 || l < 1 || w < 1 || w > PCMM_MAX_W) return PCMM_EINVAL;
+    if (m < 1 || n < 1 || l < 1 || w < 1 || w > 8 * (int)sizeof(TA)) return PCMM_EINVAL;
     if (k == 0) k = pcmm_cussen_choose_k(m, n, l, w);
     Layout L;
     if (!make_layout(L, m, n, l, w, k)) return PCMM_EINVAL;
@@ -176,6 +183,20 @@ extern "C" pcmm_status pcmm_cussen(const uint8_t* A, int m, int n, int w, const 
     return launch_exec(L, P, ctB, ctC, (uint8_t*)ws + L.plan_bytes, S, st);
 }
 
+}  // namespace
+
+extern "C" pcmm_status pcmm_cussen(const uint8_t* A, int m, int n, int w, const uint32_t* ctB, int l,
+                                   uint32_t* ctC, int k, void* ws, size_t ws_bytes,
+                                   pcmm_stream_t stream) {
+    return cussen_call(A, m, n, w, ctB, l, ctC, k, ws, ws_bytes, stream);
+}
+
+extern "C" pcmm_status pcmm_cussen16(const uint16_t* A, int m, int n, int w, const uint32_t* ctB, int l,
+                                     uint32_t* ctC, int k, void* ws, size_t ws_bytes,
+                                     pcmm_stream_t stream) {
+    return cussen_call(A, m, n, w, ctB, l, ctC, k, ws, ws_bytes, stream);
+}
+
 extern "C" size_t pcmm_cussen_plan_bytes(int m, int n, int w, int k) {
     Layout L;
     if (!make_layout(L, m, n, 1, w, k)) return 0;
@@ -184,7 +205,7 @@ extern "C" size_t pcmm_cussen_plan_bytes(int m, int n, int w, int k) {
 
 extern "C" pcmm_status pcmm_cussen_plan(const uint8_t* A, int m, int n, int w, int k, void* plan,
                                         size_t plan_bytes, pcmm_stream_t stream) {
-    if (!A || !plan || ((uintptr_t)plan & 255u)) return PCMM_EINVAL;
+    if (!A || !plan || ((uintptr_t)plan & 255u) || w > PCMM_MAX_W) return PCMM_EINVAL;
     Layout L;
     if (!make_layout(L, m, n, 1, w, k)) return PCMM_EINVAL;
     if (plan_bytes < L.plan_bytes) return PCMM_ENOMEM;

@@ -15,7 +15,8 @@ using namespace pcmm;
 
 namespace {
 
-__global__ void __launch_bounds__(128) schoolbook_kernel(const uint8_t* __restrict__ A, int m,
+template <class TA>
+__global__ void __launch_bounds__(128) schoolbook_kernel(const TA* __restrict__ A, int m,
                                                          int n, const uint4* __restrict__ ctB,
                                                          int l, uint4* __restrict__ ctC,
                                                          uint32_t amask) {
@@ -44,17 +45,29 @@ __global__ void __launch_bounds__(128) schoolbook_kernel(const uint8_t* __restri
     if (j < l) store_jac(ctC + (size_t)c * 6 * ml, ml, (size_t)i * l + j, acc);
 }
 
-}  // namespace
-
-extern "C" pcmm_status pcmm_schoolbook(const uint8_t* A, int m, int n, int w, const uint32_t* ctB,
-                                       int l, uint32_t* ctC, pcmm_stream_t stream) {
-    if (!A || !ctB || !ctC || m < 1 || n < 1 || l < 1 || w < 1 || w > PCMM_MAX_W) return PCMM_EINVAL;
+template <class TA>
+pcmm_status schoolbook_call(const TA* A, int m, int n, int w, const uint32_t* ctB, int l, uint32_t* ctC,
+                            pcmm_stream_t stream) {
+    if (!A || !ctB || !ctC || m < 1 || n < 1 || l < 1 || w < 1 || w > 8 * (int)sizeof(TA))
+        return PCMM_EINVAL;
     const long long warps = (long long)m * 2 * ((l + 31) / 32);
     const long long blocks = (warps + 3) / 4;
     if (blocks > 0x7fffffffLL) return PCMM_EUNSUPPORTED;
     ProfScope ps(KID_SCHOOLBOOK, (cudaStream_t)stream);
-    schoolbook_kernel<<<(unsigned)blocks, 128, 0, (cudaStream_t)stream>>>(
+    schoolbook_kernel<TA><<<(unsigned)blocks, 128, 0, (cudaStream_t)stream>>>(
         A, m, n, (const uint4*)ctB, l, (uint4*)ctC, (1u << w) - 1u);
     PCMM_CUDA_CHECK_LAUNCH();
     return PCMM_OK;
+}
+
+}  // namespace
+
+extern "C" pcmm_status pcmm_schoolbook(const uint8_t* A, int m, int n, int w, const uint32_t* ctB,
+                                       int l, uint32_t* ctC, pcmm_stream_t stream) {
+    return schoolbook_call(A, m, n, w, ctB, l, ctC, stream);
+}
+
+extern "C" pcmm_status pcmm_schoolbook16(const uint16_t* A, int m, int n, int w, const uint32_t* ctB,
+                                         int l, uint32_t* ctC, pcmm_stream_t stream) {
+    return schoolbook_call(A, m, n, w, ctB, l, ctC, stream);
 }

@@ -21,12 +21,13 @@ LIB_PATH = os.path.join(_HERE, "libpcmm.so")
 
 PCMM_AFF_WORDS = 32
 PCMM_JAC_WORDS = 48
+PCMM_MAX_WK = 16       # strip code width w * k, bits
 
 # Names of every exported entry point, in the order of include/pcmm.h.
 EXPORTS = (
     "pcmm_version", "pcmm_status_string", "pcmm_init", "pcmm_keytable_bytes", "pcmm_keytable",
-    "pcmm_encrypt", "pcmm_base_mul", "pcmm_schoolbook", "pcmm_cussen_choose_k", "pcmm_cussen_workspace_bytes",
-    "pcmm_cussen", "pcmm_cussen_plan_bytes", "pcmm_cussen_plan", "pcmm_cussen_exec_bytes",
+    "pcmm_encrypt", "pcmm_base_mul", "pcmm_schoolbook", "pcmm_schoolbook16", "pcmm_cussen_choose_k",
+    "pcmm_cussen_workspace_bytes", "pcmm_cussen", "pcmm_cussen16", "pcmm_cussen_plan_bytes", "pcmm_cussen_plan", "pcmm_cussen_exec_bytes",
     "pcmm_cussen_execute", "pcmm_cussen_static", "pcmm_batched_workspace_bytes", "pcmm_batched_prepare", "pcmm_batched_run",
     "pcmm_workspace_status", "pcmm_copy_columns", "pcmm_normalize", "pcmm_profile_enable",
     "pcmm_profile_read", "pcmm_kernel_count", "pcmm_kernel_name", "pcmm_test_wait", "pcmm_test_field",
@@ -62,9 +63,11 @@ def lib():
                 "pcmm_encrypt": ([vp, vp, vp, sz, vp, vp], ci),
                 "pcmm_base_mul": ([vp, sz, vp, vp], ci),
                 "pcmm_schoolbook": ([vp, ci, ci, ci, vp, ci, vp, vp], ci),
+                "pcmm_schoolbook16": ([vp, ci, ci, ci, vp, ci, vp, vp], ci),
                 "pcmm_cussen_choose_k": ([ci, ci, ci, ci], ci),
                 "pcmm_cussen_workspace_bytes": ([ci, ci, ci, ci, ci], sz),
                 "pcmm_cussen": ([vp, ci, ci, ci, vp, ci, vp, ci, vp, sz, vp], ci),
+                "pcmm_cussen16": ([vp, ci, ci, ci, vp, ci, vp, ci, vp, sz, vp], ci),
                 "pcmm_cussen_plan_bytes": ([ci, ci, ci, ci], sz),
                 "pcmm_cussen_plan": ([vp, ci, ci, ci, ci, vp, sz, vp], ci),
                 "pcmm_cussen_exec_bytes": ([ci, ci, ci, ci, ci], sz),
@@ -222,16 +225,39 @@ def public_key(sk_words: np.ndarray, device="cuda") -> np.ndarray:
 
 # ------------------------------------------------------------------ PC-MM
 
+def _wide(A) -> bool:
+    """Whether A holds 16-bit entries (torch int16 or uint16: the bits of a
+    uint16 matrix) rather than uint8."""
+    es = A.element_size()
+    if es not in (1, 2):
+        raise TypeError("A must be a uint8 or 16-bit tensor")
+    return es == 2
+
+
+def plaintext16(A_host, device="cuda"):
+    """Device copy of a host uint16 matrix, held as int16 (same bits)."""
+    torch = _torch()
+    return torch.from_numpy(np.ascontiguousarray(A_host, dtype=np.uint16).view(np.int16)).to(device)
+
+
 def schoolbook(A, ctB, l: int, w: int, out=None, stream=None):
-    """A: cuda uint8[m, n]; ctB: cuda int32[32 * n * l].  Returns the
-    Jacobian ciphertext matrix, cuda int32[48 * m * l]."""
+    """A: cuda uint8[m, n] (w <= 8) or 16-bit [m, n] (w <= 16, see
+    ``plaintext16``); ctB: cuda int32[32 * n * l].  Returns the Jacobian
+    ciphertext matrix, cuda int32[48 * m * l]."""
     torch = _torch()
     m, n = A.shape
     if out is None:
         out = torch.empty(PCMM_JAC_WORDS * m * l, dtype=torch.int32, device=A.device)
-    _check(lib().pcmm_schoolbook(_ptr(A), m, n, w, _ptr(ctB), l, _ptr(out), _stream(stream)),
-           "pcmm_schoolbook")
+    name = "pcmm_schoolbook16" if _wide(A) else "pcmm_schoolbook"
+    _check(getattr(lib(), name)(_ptr(A), m, n, w, _ptr(ctB), l, _ptr(out), _stream(stream)), name)
     return out
+
+
+def schoolbook16(A, ctB, l: int, w: int, out=None, stream=None):
+    """pcmm_schoolbook16: ``schoolbook`` with a 16-bit A."""
+    if not _wide(A):
+        raise TypeError("schoolbook16 takes a 16-bit A")
+    return schoolbook(A, ctB, l, w, out=out, stream=stream)
 
 
 def choose_k(m: int, n: int, l: int, w: int) -> int:
@@ -259,9 +285,17 @@ def cussen(A, ctB, l: int, w: int, k: int = 0, ws=None, out=None, stream=None):
         ws = workspace(m, n, l, w, k, device=A.device)
     if out is None:
         out = torch.empty(PCMM_JAC_WORDS * m * l, dtype=torch.int32, device=A.device)
-    _check(lib().pcmm_cussen(_ptr(A), m, n, w, _ptr(ctB), l, _ptr(out), k, _ptr(ws), ws.numel(),
-                             _stream(stream)), "pcmm_cussen")
+    name = "pcmm_cussen16" if _wide(A) else "pcmm_cussen"
+    _check(getattr(lib(), name)(_ptr(A), m, n, w, _ptr(ctB), l, _ptr(out), k, _ptr(ws), ws.numel(),
+                                _stream(stream)), name)
     return out
+
+
+def cussen16(A, ctB, l: int, w: int, k: int = 0, ws=None, out=None, stream=None):
+    """pcmm_cussen16: ``cussen`` with a 16-bit A (entries < 2^w, w <= 16)."""
+    if not _wide(A):
+        raise TypeError("cussen16 takes a 16-bit A")
+    return cussen(A, ctB, l, w, k=k, ws=ws, out=out, stream=stream)
 
 
 def cussen_static(A, ctB, l: int, w: int, k: int = 0, out=None, stream=None):

@@ -2,6 +2,7 @@
 function declared in include/pcmm.h (no compute call, no GPU), the host-side
 argument validation rejects bad shapes without launching anything, and the
 Python layout helpers round-trip."""
+import ctypes
 import os
 import re
 
@@ -44,11 +45,22 @@ def test_version_and_status_strings(lib):
 def test_host_validation_without_gpu(lib):
     # Invalid shapes are rejected before any CUDA call.
     assert pcmm.workspace_bytes(0, 4, 4, 4, 1) == 0
-    assert pcmm.workspace_bytes(4, 4, 4, 9, 1) == 0
-    assert pcmm.workspace_bytes(4, 4, 4, 4, 4) == 0   # w * k = 16 > 12
-    assert pcmm.workspace_bytes(4, 4, 4, 4, 3) > 0
+    assert pcmm.workspace_bytes(4, 4, 4, 17, 1) == 0   # w > 16
+    assert pcmm.workspace_bytes(4, 4, 4, 9, 2) == 0    # w * k = 18 > 16
+    assert pcmm.workspace_bytes(4, 4, 4, 4, 5) == 0    # w * k = 20 > 16
+    assert pcmm.workspace_bytes(4, 4, 4, 4, 4) > 0
+    assert pcmm.workspace_bytes(4, 4, 4, 16, 1) > 0
     assert lib.pcmm_cussen(None, 4, 4, 4, None, 4, None, 1, None, 0, None) == 1
+    assert lib.pcmm_cussen16(None, 4, 4, 12, None, 4, None, 1, None, 0, None) == 1
     assert lib.pcmm_schoolbook(None, 4, 4, 4, None, 4, None, None) == 1
+    assert lib.pcmm_schoolbook16(None, 4, 4, 12, None, 4, None, None) == 1
+    # The uint8 entry points reject widths that do not fit a byte (checked
+    # before any pointer is used; the dummy pointers are never dereferenced).
+    d = ctypes.c_void_p(256)
+    assert lib.pcmm_cussen(d, 4, 4, 9, d, 4, d, 1, d, 1 << 20, None) == 1
+    assert lib.pcmm_schoolbook(d, 4, 4, 9, d, 4, d, None) == 1
+    assert lib.pcmm_cussen16(d, 4, 4, 17, d, 4, d, 1, d, 1 << 20, None) == 1
+    assert lib.pcmm_cussen16(d, 4, 4, 9, d, 4, d, 2, d, 1 << 20, None) == 1
     assert lib.pcmm_normalize(None, 4, None, None) == 1
 
 
@@ -57,9 +69,12 @@ def test_cost_model_choices(lib):
     assert pcmm.choose_k(1024, 1024, 256, 8) == 1
     assert pcmm.choose_k(1024, 1024, 256, 4) >= 2
     assert pcmm.choose_k(1024, 1024, 256, 1) >= 4
-    for w in range(1, 9):
+    for w in range(1, 17):
         k = pcmm.choose_k(100, 50, 20, w)
-        assert 1 <= k and w * k <= 12
+        assert 1 <= k and w * k <= 16
+    assert pcmm.choose_k(1024, 1024, 256, 12) == 1
+    assert pcmm.choose_k(1024, 1024, 256, 16) == 1
+    assert pcmm.choose_k(100, 50, 20, 17) == 0
 
 
 def test_layout_helpers_round_trip():

@@ -68,7 +68,7 @@ def test_ragged_multi_tile_shapes(dev, w):
     m, n, l = 70, 37, 45
     pr, A, ctB = _problem(dev, 500 + w, m, n, l, w)
     want = _want(pr)
-    ks = sorted({1, 2, 12 // w, 0} - {k for k in (2, 12 // w) if w * k > 12})
+    ks = sorted({1, 2, 12 // w, 16 // w, 0} - {k for k in (2, 12 // w, 16 // w) if w * k > 16})
     for k in ks:
         got = run_affine(lambda: pcmm.cussen(A, ctB, l, w, k=k), m * l)
         assert mismatches(got, want) == 0, (w, k)
@@ -173,7 +173,7 @@ def test_workspace_too_small_and_bad_arguments(dev):
     assert ei.value.status == 2
     ws = pcmm.workspace(m, n, l, w, 1, device=dev)
     with pytest.raises(pcmm.PcmmError) as ei:
-        pcmm.cussen(A, ctB, l, w, k=4, ws=ws)      # w * k = 16 > 12
+        pcmm.cussen(A, ctB, l, w, k=5, ws=ws)      # w * k = 20 > 16
     assert ei.value.status == 1
     with pytest.raises(pcmm.PcmmError):
         pcmm.schoolbook(A, ctB, l, 9)
