@@ -437,26 +437,31 @@ __device__ __forceinline__ bool fe_is_one(const fe& a) {
     return z == 0u;
 }
 
-// Normalises E lane-planar Jacobian entries to canonical affine (infinity ->
-// (0, 0)) and hands entry e to store(e, point).  Montgomery's simultaneous
-// inversion: per-lane prefix products of the Z's (kept in pref), then one
-// warp-wide inversion.  When every Z in the warp is already 1 the entries
-// are copied without any inversion.  All 32 lanes call with the same E.
+// One forward step of the simultaneous inversion, for loops that produce
+// lane-planar Jacobian entries: acc *= Z_e (a zero Z, i.e. infinity, counts
+// as 1), prefix product stored as entry e of pref; ones tracks whether every
+// Z so far is 1.
+__device__ __forceinline__ void lp_pref_step(fe& acc, bool& ones, const fe& Z, uint4* pref, int e,
+                                             unsigned lane) {
+    fe z = Z;
+    ones &= fe_is_one(z);
+    if (fe_is_zero(z)) fe_one(z);
+    acc = fmul(acc, z);
+    lp_store_fe(pref, e, lane, acc);
+}
+
+// Backward half of the normalisation of E lane-planar Jacobian entries to
+// canonical affine (infinity -> (0, 0)), each handed to store(e, point):
+// pref holds the per-lane prefix products of the Z's and acc their total
+// (lp_pref_step).  One warp-wide inversion; when every Z in the warp is 1 the
+// entries are copied without any.  The loads of entry e - 2 are prefetched
+// into L2 while entry e is converted (lanes 0-23: the 24 lines of the
+// Jacobian entry, lanes 24-31: the 8 lines of its prefix product).  All 32
+// lanes call with the same E.
 template <class Store>
-__device__ __forceinline__ void lp_normalize(const uint4* src, int E, uint4* pref, unsigned lane,
-                                             Store store) {
+__device__ __forceinline__ void lp_normalize_back(const uint4* src, int E, const uint4* pref, unsigned lane,
+                                                  fe acc, bool ones, Store store) {
     if (E <= 0) return;
-    bool ones = true;
-    fe acc;
-    fe_one(acc);
-    for (int e = 0; e < E; e++) {
-        fe z;
-        lp_load_z(z, src, e, lane);
-        ones &= fe_is_one(z);
-        if (fe_is_zero(z)) fe_one(z);
-        acc = fmul(acc, z);
-        lp_store_fe(pref, e, lane, acc);
-    }
     if (__all_sync(0xffffffffu, ones)) {
         for (int e = 0; e < E; e++) {
             jac Pe;
@@ -471,6 +476,12 @@ __device__ __forceinline__ void lp_normalize(const uint4* src, int E, uint4* pre
     fe inv;
     warp_inverse(inv, acc);
     for (int e = E - 1; e >= 0; e--) {
+        if (e >= 2) {
+            const char* line = lane < 24u ? (const char*)(src + (size_t)(e - 2) * 192) + lane * 128u
+                                          : (e >= 3 ? (const char*)(pref + (size_t)(e - 3) * 64) + (lane - 24u) * 128u
+                                                    : nullptr);
+            if (line) asm volatile("prefetch.global.L2 [%0];" ::"l"(line));
+        }
         fe zinv;
         if (e > 0) {
             fe pr;
@@ -494,6 +505,22 @@ __device__ __forceinline__ void lp_normalize(const uint4* src, int E, uint4* pre
         }
         store(e, out);
     }
+}
+
+// Normalises E lane-planar Jacobian entries already in scratch (both passes).
+template <class Store>
+__device__ __forceinline__ void lp_normalize(const uint4* src, int E, uint4* pref, unsigned lane,
+                                             Store store) {
+    if (E <= 0) return;
+    bool ones = true;
+    fe acc;
+    fe_one(acc);
+    for (int e = 0; e < E; e++) {
+        fe z;
+        lp_load_z(z, src, e, lane);
+        lp_pref_step(acc, ones, z, pref, e, lane);
+    }
+    lp_normalize_back(src, E, pref, lane, acc, ones, store);
 }
 
 // One warp per (strip, component c, 32 output columns); all lanes follow the
@@ -552,6 +579,11 @@ __device__ __forceinline__ void table_item(const TableArgs& a, const PlanPtrs& P
         }
         uint4* alt = levB;
         // Levels N-1..2: un-sort by the tracking pointers, then prefix sums.
+        // The last of them (level 2) also takes the forward pass of its
+        // normalisation.
+        fe pacc;
+        bool pones = true;
+        fe_one(pacc);
         for (int lev = NLEV - 1; lev >= 2; lev--) {
             const uint16_t* ptr = col_level_ptr(P, col, lev);
             jac acc, D;
@@ -560,13 +592,20 @@ __device__ __forceinline__ void table_item(const TableArgs& a, const PlanPtrs& P
                 lp_load_jac(D, src, ptr[e], lane);
                 jac_add(acc, D);
                 lp_store_jac(alt, e, lane, acc);
+                if (lev == 2) lp_pref_step(pacc, pones, acc.Z, pref, e, lane);
             }
             uint4* tmp = src; src = alt; alt = tmp;
         }
         // Level 2 (multiples of the level-1 differences) to affine, so that
         // the level-1 prefix sums are mixed additions.
-        lp_normalize(src, lens[1], pref, lane, [&](int e, const aff& q) { lp_store_aff(l2aff, e, lane, q); });
-        // Level 1: the multiples of the column's sorted distinct values.
+        auto store_l2 = [&](int e, const aff& q) { lp_store_aff(l2aff, e, lane, q); };
+        if (NLEV > 2) lp_normalize_back(src, lens[1], pref, lane, pacc, pones, store_l2);
+        else lp_normalize(src, lens[1], pref, lane, store_l2);
+        // Level 1: the multiples of the column's sorted distinct values,
+        // with the forward pass of their normalisation.
+        fe cacc;
+        bool cones = true;
+        fe_one(cacc);
         {
             const uint16_t* ptr = col_level_ptr(P, col, 1);
             jac acc;
@@ -576,15 +615,17 @@ __device__ __forceinline__ void table_item(const TableArgs& a, const PlanPtrs& P
                 lp_load_aff(D, l2aff, ptr[e], lane);
                 jac_madd(acc, D);
                 lp_store_jac(coltab, e, lane, acc);
+                lp_pref_step(cacc, cones, acc.Z, pref, e, lane);
             }
         }
         if (a.k == 1) {
-            // The column table is the strip table.
-            lp_normalize(coltab, E, pref, lane, store_table);
+            // The column table is the strip table (E = lens[0] entries).
+            lp_normalize_back(coltab, E, pref, lane, cacc, cones, store_table);
             return;
         }
         uint4* ca = colaff + (size_t)t * a.n1max * 128;
-        lp_normalize(coltab, lens[0], pref, lane, [&](int e, const aff& q) { lp_store_aff(ca, e, lane, q); });
+        lp_normalize_back(coltab, lens[0], pref, lane, cacc, cones,
+                          [&](int e, const aff& q) { lp_store_aff(ca, e, lane, q); });
     }
     if (bad) {
         if (lane == 0) atomicOr(P.status, DEV_ERR_PLAN);

@@ -140,3 +140,25 @@ def test_wide_full_size_sampled(dev, w):
     pairs = np.concatenate([pairs, [[0, 0], [m - 1, l - 1]]])
     want = oracle.closed_form(pr["A"], pr["r"], pr["sk"], pr["B"], pairs=pairs)
     assert mismatches(got[pairs[:, 0] * l + pairs[:, 1]], want) == 0
+
+
+def test_wide_maximum_rows(dev):
+    # 70000 rows of 16-bit values: about 43000 distinct values per column, so
+    # the level-1 lists, tracking pointers, ranks and strip tables run close
+    # to the 2^16 - 1 entries the 16-bit plan arrays allow.
+    m, n, l, w = 70000, 2, 1, 16
+    pr, A, ctB = _problem(dev, 2000, m, n, l, w)
+    ws = pcmm.workspace(m, n, l, w, 1, device=dev)
+    jac = pcmm.cussen16(A, ctB, l, w, k=1, ws=ws)
+    aff = pcmm.normalize(jac, m * l)
+    torch.cuda.synchronize()
+    assert pcmm.workspace_status(ws) == 0
+    got = pcmm.planar_to_ct(pcmm.to_host_words(aff), m * l)
+    rng = np.random.default_rng(2001)
+    rows = np.concatenate([rng.integers(0, m, 120), [0, m - 1]])
+    # Rows holding the smallest and largest values of each column too.
+    for c in range(n):
+        rows = np.concatenate([rows, [int(np.argmin(pr["A"][:, c])), int(np.argmax(pr["A"][:, c]))]])
+    pairs = np.stack([rows, np.zeros_like(rows)], axis=1)
+    want = oracle.closed_form(pr["A"], pr["r"], pr["sk"], pr["B"], pairs=pairs)
+    assert mismatches(got[rows], want) == 0
