@@ -48,9 +48,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-schoolbook", action="store_true")
-    ap.add_argument("--workload", choices=["large", "serving", "batched"], default="large",
+    ap.add_argument("--workload", choices=["large", "serving", "batched", "sweep"], default="large",
                     help="large: the single large PC-MM (the headline line); serving: Poisson "
-                         "request sweep of encrypted linear layers; batched: 64 uneven instances")
+                         "request sweep of encrypted linear layers; batched: 64 uneven instances; "
+                         "sweep: square PC-MM over n and w, Cussen beside schoolbook")
+    ap.add_argument("--sweep-n", default="128,256,512,1024,2048")
+    ap.add_argument("--sweep-widths", default="1,2,3,4,5,6,7,8,12,16")
     ap.add_argument("--rates", default="10,20,50,100,200,500,1000,2000")
     ap.add_argument("--seconds", type=float, default=2.0, help="arrival window per rate (serving)")
     return ap.parse_args()
@@ -483,6 +486,83 @@ def run_batched(args, dist):
             "autotune_s": t_tune, "steps": args.steps, "n_gpus": 1}
 
 
+def run_sweep(args, dist):
+    """Square PC-MM sweep: A n x n with uniform w-bit entries times Enc(B)
+    n x n (8-bit messages) for every n and w asked for.  Per (n, w): the
+    Cussen wall time (cost-model k, best of two calls after a warm-up), its
+    point additions per second and IMAD fraction, and the schoolbook wall
+    time on the same GPU.  The schoolbook is timed on a slice of rows sized
+    to about 4e9 point operations and scaled to n rows: every output row is
+    an independent sum of the same cost."""
+    import torch
+
+    from paper_2504_14497_gb300 import build, counts, inputs, pcmm
+
+    build.build()
+    torch.cuda.set_device(dist.local)
+    dev = torch.device("cuda", dist.local)
+    pcmm.init(dist.local)
+    props = torch.cuda.get_device_properties(dev)
+    clocks = ClockSampler(dist.local)
+    clocks.start()
+    seed = 2504144970 + 3
+    cur = torch.cuda.current_stream()
+
+    def timed(fn, reps=2):
+        fn()
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(cur)
+            fn()
+            e1.record(cur)
+            e1.synchronize()
+            t = e0.elapsed_time(e1)
+            best = t if best is None else min(best, t)
+        return best
+
+    rows = []
+    for n in (int(x) for x in args.sweep_n.split(",")):
+        pr = inputs.pcmm_problem(seed, n, n, n, 1)
+        tab = pcmm.keytable(pcmm.public_key(pr["sk"], device=dev), device=dev)
+        ctB = pcmm.encrypt(tab, torch.from_numpy(pr["B"].reshape(-1)).to(dev),
+                           pcmm.to_device_words(pcmm.scalars_to_planar(pr["r"]), dev))
+        out = torch.empty(48 * n * n, dtype=torch.int32, device=dev)
+        for w in (int(x) for x in args.sweep_widths.split(",")):
+            A_h = inputs.plaintext_matrix(seed, n, n, w)
+            A = _host_plaintext(A_h).to(dev)
+            k = pcmm.choose_k(n, n, n, w)
+            ws = pcmm.workspace(n, n, n, w, k, device=dev)
+            ms = timed(lambda: pcmm.cussen(A, ctB, n, w, k=k, ws=ws, out=out))
+            if pcmm.workspace_status(ws) != 0:
+                raise RuntimeError(f"device status at n={n} w={w}")
+            del ws
+            c = counts.cussen_counts(A_h, w, k, n)
+            ops = counts.point_ops(c)
+            imad = counts.gather_imad(c) + counts.table_imad(c)
+            ops_row = 2.0 * n * n * (1.5 * w + 1)          # schoolbook point operations per row
+            ms_rows = int(min(n, max(8, 4e9 // ops_row)))
+            sb = timed(lambda: pcmm.schoolbook(A[:ms_rows], ctB, n, w, out=out), reps=1)
+            sb_full = sb * n / ms_rows
+            rows.append({"n": n, "w": w, "k": k, "cussen_ms": ms, "point_adds_per_s": ops / (ms / 1e3),
+                         "imad": imad, "schoolbook_ms": sb_full,
+                         "schoolbook_rows_timed": ms_rows, "speedup_vs_schoolbook": sb_full / ms})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+            torch.cuda.empty_cache()
+        del ctB, out
+        torch.cuda.empty_cache()
+    clk = clocks.stop()
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak = props.multi_processor_count * IMAD_PER_SM_PER_CLK * sm_max * 1e6
+    for r in rows:
+        r["imad_frac"] = r.pop("imad") / (r["cussen_ms"] / 1e3) / peak
+    return {"workload": "sweep: square PC-MM A n x n (uniform w-bit) x Enc(B) n x n (8-bit messages), "
+                        "Cussen with cost-model k beside schoolbook, one PC-MM per launch",
+            "metric": "Cussen PC-MM wall time and point-adds/s per (n, w)", "unit": "ms",
+            "peak_imad_per_s": peak, "clocks": clk, "rows": rows, "n_gpus": 1, "data": "synthetic (seeded)"}
+
+
 SERVING_MODELS = {"mlp_784": (256, 784), "mlp_256": (128, 256), "mlp_out": (10, 128)}
 
 
@@ -585,6 +665,8 @@ def main():
             out = run_serving(args, dist)
         elif args.workload == "batched":
             out = run_batched(args, dist)
+        elif args.workload == "sweep":
+            out = run_sweep(args, dist)
         else:
             out = run_ours(args, dist)
         if dist.rank == 0 and out is not None:

@@ -54,6 +54,18 @@ def uniform_scalars(rng: np.random.Generator, shape) -> np.ndarray:
     return out.reshape(shape + (8,))
 
 
+def _plaintext(gen, m: int, n: int, w: int) -> np.ndarray:
+    adt = np.uint8 if w <= 8 else np.uint16
+    return gen.integers(0, 1 << w, size=(m, n), dtype=adt) if m * n else np.zeros((m, n), adt)
+
+
+def plaintext_matrix(seed: int, m: int, n: int, w: int) -> np.ndarray:
+    """The A of pcmm_problem(seed, m, n, l, w, ...), drawn alone."""
+    if not 1 <= w <= 16:
+        raise ValueError("w must be in [1, 16]")
+    return _plaintext(streams(seed)["A"], m, n, w)
+
+
 def pcmm_problem(seed: int, m: int, n: int, l: int, w: int, msg_bits: int = 8) -> dict:
     """One PC-MM instance: plaintext A (m x n, w-bit; uint8 for w <= 8,
     uint16 for 8 < w <= 16), message matrix B (n x l, msg_bits-bit), secret
@@ -62,8 +74,7 @@ def pcmm_problem(seed: int, m: int, n: int, l: int, w: int, msg_bits: int = 8) -
         raise ValueError("w must be in [1, 16]")
     s = streams(seed)
     sk = uniform_scalars(s["sk"], (1,))[0]
-    adt = np.uint8 if w <= 8 else np.uint16
-    A = s["A"].integers(0, 1 << w, size=(m, n), dtype=adt) if m * n else np.zeros((m, n), adt)
+    A = _plaintext(s["A"], m, n, w)
     B = s["B"].integers(0, 1 << msg_bits, size=(n, l), dtype=np.uint8) if n * l else np.zeros((n, l), np.uint8)
     r = uniform_scalars(s["r"], (n, l))
     return {"sk": sk, "A": A, "B": B, "r": r, "m": m, "n": n, "l": l, "w": w}

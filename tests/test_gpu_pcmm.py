@@ -215,6 +215,28 @@ def test_full_size_sampled(dev, w):
         assert oracle.on_curve(ct[0]) and oracle.on_curve(ct[1])
 
 
+@pytest.mark.parametrize("n,w", [(128, 3), (512, 5), (2048, 7), (2048, 1)])
+def test_sweep_config_sampled(dev, n, w):
+    # The square sweep workload (A n x n, Enc(B) n x n), as bench.py's sweep
+    # mode runs it: cost-model k, sampled outputs against the closed form.
+    seed = inputs.SEED_BASE + 3
+    pr = inputs.pcmm_problem(seed, n, n, n, 1)
+    Ah = inputs.plaintext_matrix(seed, n, n, w)
+    ctB = encrypt_gpu(dev, pr)
+    A = torch.from_numpy(Ah).to(dev)
+    k = pcmm.choose_k(n, n, n, w)
+    ws = pcmm.workspace(n, n, n, w, k, device=dev)
+    aff = pcmm.normalize(pcmm.cussen(A, ctB, n, w, k=k, ws=ws), n * n)
+    torch.cuda.synchronize()
+    assert pcmm.workspace_status(ws) == 0
+    got = pcmm.planar_to_ct(pcmm.to_host_words(aff), n * n)
+    rng = np.random.default_rng(n + w)
+    pairs = np.stack([rng.integers(0, n, 48), rng.integers(0, n, 48)], axis=1)
+    pairs = np.concatenate([pairs, [[0, 0], [n - 1, n - 1]]])
+    want = oracle.closed_form(Ah, pr["r"], pr["sk"], pr["B"], pairs=pairs)
+    assert mismatches(got[pairs[:, 0] * n + pairs[:, 1]], want) == 0
+
+
 def test_base_mul_keygen_matches_oracle(dev):
     s = inputs.streams(123)
     sk = inputs.uniform_scalars(s["sk"], (300,))
