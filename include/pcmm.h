@@ -243,8 +243,11 @@ typedef struct {
 } pcmm_batch_info;
 
 /* Workspace bytes for a batch on the current device (0 for invalid input).
- * max_strips: strips per pass of an instance (its column strips are built and
- * gathered max_strips at a time, two passes' tables resident); 0 = 64. */
+ * max_strips: upper bound on the strips per pass of an instance (its column
+ * strips are built and gathered a pass at a time, two passes' tables
+ * resident); 0 = the library's choice: at least 1024 table warps per pass
+ * (and at least 64 strips while both buffers fit in 256 MB), at most 2 GB
+ * per table buffer. */
 size_t pcmm_batched_workspace_bytes(const pcmm_problem *probs, int count, int max_strips);
 
 /* Sizes every instance, lays out the workspace (plans, two table buffers per

@@ -755,6 +755,8 @@ struct GatherArgs {
     const uint4* table;
     size_t table_points;
     uint4* ctC;            // Jacobian ciphertext matrix m x l
+    int parts;             // warps per output splitting the chunk's strips (1: accumulate into ctC)
+    uint4* partial;        // parts > 1: Jacobian partial sums, parts matrices laid out like ctC
 };
 
 // Accumulation of one warp item (output row i, component c, 32 columns) over
@@ -766,20 +768,27 @@ __device__ __forceinline__ void gather_item(const GatherArgs& a, const PlanPtrs&
     // Rows innermost: the warps resident at a time cover every row of a few
     // column blocks, so each strip's table region is fetched once per block
     // while those warps walk the strips together.
+    // With parts > 1 (small outputs), warp gw / (m 2 njb) takes part p of
+    // the chunk's strips and leaves its partial sum for combine_kernel.
     const unsigned lane = threadIdx.x & 31u;
+    const long long per_part = (long long)a.m * 2 * a.njb;
+    const int part = (int)(gw / per_part);
+    gw %= per_part;
     const int i = (int)(gw % a.m);
     const int rem = (int)(gw / a.m);
     const int c = rem / a.njb, jb = rem % a.njb;
     const int j = jb * 32 + (int)lane;
     const size_t ml = (size_t)a.m * a.l;
-    uint4* Cc = a.ctC + (size_t)c * 6 * ml;
+    uint4* Cc = (a.parts > 1 ? a.partial + (size_t)part * 12 * ml : a.ctC) + (size_t)c * 6 * ml;
     jac acc;
-    if (a.first || j >= a.l) jac_set_inf(acc);
+    if (a.first || a.parts > 1 || j >= a.l) jac_set_inf(acc);
     else if (CG) load_jac_cg(acc, Cc, ml, (size_t)i * a.l + j);
     else load_jac(acc, Cc, ml, (size_t)i * a.l + j);
     const uint16_t* rk = P.rank + (size_t)a.s0 * a.m + i;
     aff T;
-    for (int sl = 0; sl < a.nstrips_chunk; sl++) {
+    const int s_lo = (int)((long long)a.nstrips_chunk * part / a.parts);
+    const int s_hi = (int)((long long)a.nstrips_chunk * (part + 1) / a.parts);
+    for (int sl = s_lo; sl < s_hi; sl++) {
         const uint16_t code = rk[(size_t)sl * a.m];
         if (code == NO_RANK) continue;
         const size_t ti = (((size_t)sl * a.emax + code) * 2 + c) * a.lp + j;

@@ -121,6 +121,7 @@ __global__ void __launch_bounds__(BATCH_THREADS) batched_kernel(const Inst* __re
             if (!__shfl_sync(0xffffffffu, ok, 0)) break;
             GatherArgs ga;
             ga.m = I.m; ga.l = I.l; ga.lp = I.lp; ga.njb = I.njb; ga.emax = I.emax;
+            ga.parts = 1; ga.partial = nullptr;
             ga.s0 = s0; ga.nstrips_chunk = sc;
             ga.first = (sg.chunk == 0);
             ga.table = tbuf;
@@ -147,10 +148,22 @@ struct HostLayout {
 
 // Strips per pass of one instance: at most max_strips (long gathers), and
 // few enough that the two table buffers stay near `table_budget` bytes.
-int strips_per_pass(const Layout& L, size_t table_budget, int max_strips) {
+// Strips per pass of one instance.  An instance's passes run one after
+// another, so a pass should hold enough table warps to keep the queue busy
+// (PASS_ITEMS) while its two table buffers stay within 2 x BUFFER_CAP bytes:
+// at least min(64 strips, 256 MB for both buffers), raised to PASS_ITEMS
+// table items, capped by BUFFER_CAP per buffer and by max_strips when given.
+const size_t PASS_ITEMS = 1024;
+const size_t BUFFER_CAP = (size_t)2 << 30;
+
+int strips_per_pass(const Layout& L, int max_strips) {
     const size_t per_strip = align256(L.table_points_per_strip * 64);
-    size_t S = table_budget / (2 * per_strip);
-    if (S > (size_t)max_strips) S = max_strips;
+    size_t S = ((size_t)256 << 20) / (2 * per_strip);
+    if (S > 64) S = 64;
+    const size_t by_items = (PASS_ITEMS + L.items_per_strip - 1) / L.items_per_strip;
+    if (S < by_items) S = by_items;
+    if (S > BUFFER_CAP / per_strip) S = BUFFER_CAP / per_strip;
+    if (max_strips > 0 && S > (size_t)max_strips) S = max_strips;
     if (S > (size_t)L.nstrips) S = L.nstrips;
     return S < 1 ? 1 : (int)S;
 }
@@ -158,7 +171,6 @@ int strips_per_pass(const Layout& L, size_t table_budget, int max_strips) {
 pcmm_status build_layout(const pcmm_problem* probs, int count, int max_strips, int grid,
                          HostLayout& H) {
     if (!probs || count < 1 || grid < 1 || max_strips < 0) return PCMM_EINVAL;
-    if (max_strips == 0) max_strips = 64;
     H = HostLayout();
     H.grid = grid;
     std::vector<Layout> Ls(count);
@@ -176,14 +188,13 @@ pcmm_status build_layout(const pcmm_problem* probs, int count, int max_strips, i
         off = align256(off + Ls[i].plan_bytes);
     }
     // Table buffers (two per instance).
-    const size_t table_budget = (size_t)256 << 20;
     std::vector<size_t> tab_off(count);
     H.insts.resize(count);
     int ctr = 0;
     for (int i = 0; i < count; i++) {
         const Layout& L = Ls[i];
         Inst& I = H.insts[i];
-        I.S = strips_per_pass(L, table_budget, max_strips);
+        I.S = strips_per_pass(L, max_strips);
         I.nchunks = (L.nstrips + I.S - 1) / I.S;
         I.table_points = (size_t)I.S * L.table_points_per_strip;
         tab_off[i] = off;

@@ -65,8 +65,27 @@ __global__ void __launch_bounds__(128, PCMM_TABLE_MINBLOCKS) table_kernel(TableA
 
 __global__ void __launch_bounds__(128, PCMM_GATHER_MINBLOCKS) gather_kernel(GatherArgs a, PlanPtrs P) {
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (gw >= (long long)a.m * 2 * a.njb) return;
+    if (gw >= (long long)a.m * 2 * a.njb * a.parts) return;
     gather_item<false>(a, P, gw);
+}
+
+// Adds the parts partial sums of every output point (and, after the first
+// pass, the accumulated value) into ctC: one thread per point.
+__global__ void __launch_bounds__(128) combine_kernel(const uint4* __restrict__ partial, int parts,
+                                                      uint4* __restrict__ ctC, size_t ml, bool first) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 2 * ml) return;
+    const size_t c = t / ml, idx = t % ml;
+    uint4* Cc = ctC + c * 6 * ml;
+    jac acc;
+    if (first) jac_set_inf(acc);
+    else load_jac(acc, Cc, ml, idx);
+    for (int p = 0; p < parts; p++) {
+        jac Q;
+        load_jac(Q, partial + (size_t)p * 12 * ml + c * 6 * ml, ml, idx);
+        jac_add(acc, Q);
+    }
+    store_jac(Cc, ml, idx, acc);
 }
 
 }  // namespace
@@ -88,16 +107,6 @@ extern "C" int pcmm_cussen_choose_k(int m, int n, int l, int w) {
 #endif
 static const size_t TARGET_ITEMS = PCMM_TARGET_ITEMS;
 
-extern "C" size_t pcmm_cussen_workspace_bytes(int m, int n, int l, int w, int k) {
-    if (k == 0) k = pcmm_cussen_choose_k(m, n, l, w);
-    Layout L;
-    if (!make_layout(L, m, n, l, w, k)) return 0;
-    size_t S = (TARGET_ITEMS + L.items_per_strip - 1) / L.items_per_strip;
-    if (S > (size_t)L.nstrips) S = L.nstrips;
-    if (S < 1) S = 1;
-    return L.plan_bytes + S * L.per_strip_bytes;
-}
-
 namespace {
 size_t default_strips(const Layout& L);
 }
@@ -115,12 +124,35 @@ pcmm_status launch_plan(const Layout& L, const TA* A, const PlanPtrs& P, cudaStr
     return PCMM_OK;
 }
 
+// Warps per output for the gather of a pass of S strips: when the outputs
+// alone give fewer than GATHER_WARPS_TARGET warps (about four waves of the
+// gather on 152 SMs), each output's strips are split into up to 32 parts of
+// at least 16 strips, and combine_kernel adds the partial sums (one full
+// addition per part against at least 16 mixed additions).
+const long long GATHER_WARPS_TARGET = 12288;
+
+int gather_parts(const Layout& L, size_t S) {
+    const long long warps = (long long)L.m * 2 * L.njb;
+    if (warps >= GATHER_WARPS_TARGET) return 1;
+    long long parts = (GATHER_WARPS_TARGET + warps - 1) / warps;
+    const long long by_strips = (long long)S / 16;
+    if (parts > by_strips) parts = by_strips;
+    if (parts > 32) parts = 32;
+    return parts < 1 ? 1 : (int)parts;
+}
+
+size_t partial_bytes(const Layout& L, int parts) {
+    return parts > 1 ? align256((size_t)parts * 2 * L.m * L.l * 96) : 0;
+}
+
 // Table build and gather over chunks of S strips, using the scratch area at
-// `chunk` (S * per_strip_bytes bytes).
+// `chunk` (S * per_strip_bytes bytes) and, when parts > 1, the partial sums
+// at `partial` (partial_bytes(L, parts) bytes).
 pcmm_status launch_exec(const Layout& L, const PlanPtrs& P, const uint32_t* ctB, uint32_t* ctC,
-                        uint8_t* chunk, size_t S, cudaStream_t st) {
+                        uint8_t* chunk, size_t S, uint8_t* partial, int parts, cudaStream_t st) {
     uint4* scratch = (uint4*)chunk;
     uint4* table = (uint4*)(chunk + align256(S * L.items_per_strip * L.item_u4 * 16));
+    const size_t ml = (size_t)L.m * L.l;
     for (int s0 = 0; s0 < L.nstrips; s0 += (int)S) {
         const int sc = (int)((size_t)(L.nstrips - s0) < S ? (size_t)(L.nstrips - s0) : S);
         TableArgs ta;
@@ -145,10 +177,20 @@ pcmm_status launch_exec(const Layout& L, const PlanPtrs& P, const uint32_t* ctB,
         ga.table = table;
         ga.table_points = ta.table_points;
         ga.ctC = (uint4*)ctC;
-        const long long warps = (long long)L.m * 2 * L.njb;
+        // A short last chunk may take fewer parts than the buffer holds.
+        const int pc = parts > 1 ? (sc / 16 < parts ? (sc / 16 > 1 ? sc / 16 : 1) : parts) : 1;
+        ga.parts = pc;
+        ga.partial = (uint4*)partial;
+        const long long warps = (long long)L.m * 2 * L.njb * pc;
         {
             ProfScope ps(KID_GATHER, st);
             gather_kernel<<<(unsigned)((warps + 3) / 4), 128, 0, st>>>(ga, P);
+        }
+        PCMM_CUDA_CHECK_LAUNCH();
+        if (pc > 1) {
+            ProfScope ps(KID_COMBINE, st);
+            combine_kernel<<<(unsigned)((2 * ml + 127) / 128), 128, 0, st>>>((const uint4*)partial, pc,
+                                                                           (uint4*)ctC, ml, s0 == 0);
         }
         PCMM_CUDA_CHECK_LAUNCH();
     }
@@ -159,6 +201,33 @@ size_t default_strips(const Layout& L) {
     size_t S = (TARGET_ITEMS + L.items_per_strip - 1) / L.items_per_strip;
     if (S > (size_t)L.nstrips) S = L.nstrips;
     return S < 1 ? 1 : S;
+}
+
+// Bytes of execution workspace (beyond the plan) the default configuration
+// uses: the gather's partial sums, then passes of default_strips strips.
+size_t default_exec_bytes(const Layout& L) {
+    const size_t S = default_strips(L);
+    return partial_bytes(L, gather_parts(L, S)) + S * L.per_strip_bytes;
+}
+
+// Splits `avail` bytes of execution workspace into the partial sums (when
+// the gather splits its strips) and passes of S strips; the partial sums are
+// dropped when both do not fit.  False when not even one strip fits.
+bool exec_space(const Layout& L, size_t avail, size_t& S, int& parts, size_t& pbytes) {
+    parts = gather_parts(L, default_strips(L));
+    pbytes = partial_bytes(L, parts);
+    if (parts > 1 && avail >= pbytes + L.per_strip_bytes) {
+        S = (avail - pbytes) / L.per_strip_bytes;
+    } else {
+        parts = 1;
+        pbytes = 0;
+        if (avail < L.per_strip_bytes) return false;
+        S = avail / L.per_strip_bytes;
+    }
+    if (S > (size_t)L.nstrips) S = L.nstrips;
+    const int ps = gather_parts(L, S);
+    if (ps < parts) parts = ps;
+    return true;
 }
 
 }  // namespace
@@ -173,17 +242,26 @@ pcmm_status cussen_call(const TA* A, int m, int n, int w, const uint32_t* ctB, i
     if (k == 0) k = pcmm_cussen_choose_k(m, n, l, w);
     Layout L;
     if (!make_layout(L, m, n, l, w, k)) return PCMM_EINVAL;
-    if (ws_bytes < L.plan_bytes + L.per_strip_bytes) return PCMM_ENOMEM;
-    size_t S = (ws_bytes - L.plan_bytes) / L.per_strip_bytes;
-    if (S > (size_t)L.nstrips) S = L.nstrips;
+    if (ws_bytes < L.plan_bytes) return PCMM_ENOMEM;
+    size_t S, pbytes;
+    int parts;
+    if (!exec_space(L, ws_bytes - L.plan_bytes, S, parts, pbytes)) return PCMM_ENOMEM;
     cudaStream_t st = (cudaStream_t)stream;
     PlanPtrs P = plan_ptrs(L, ws);
     pcmm_status rc = launch_plan(L, A, P, st);
     if (rc != PCMM_OK) return rc;
-    return launch_exec(L, P, ctB, ctC, (uint8_t*)ws + L.plan_bytes, S, st);
+    uint8_t* partial = (uint8_t*)ws + L.plan_bytes;
+    return launch_exec(L, P, ctB, ctC, partial + pbytes, S, partial, parts, st);
 }
 
 }  // namespace
+
+extern "C" size_t pcmm_cussen_workspace_bytes(int m, int n, int l, int w, int k) {
+    if (k == 0) k = pcmm_cussen_choose_k(m, n, l, w);
+    Layout L;
+    if (!make_layout(L, m, n, l, w, k)) return 0;
+    return L.plan_bytes + default_exec_bytes(L);
+}
 
 extern "C" pcmm_status pcmm_cussen(const uint8_t* A, int m, int n, int w, const uint32_t* ctB, int l,
                                    uint32_t* ctC, int k, void* ws, size_t ws_bytes,
@@ -215,7 +293,7 @@ extern "C" pcmm_status pcmm_cussen_plan(const uint8_t* A, int m, int n, int w, i
 extern "C" size_t pcmm_cussen_exec_bytes(int m, int n, int l, int w, int k) {
     Layout L;
     if (!make_layout(L, m, n, l, w, k)) return 0;
-    return default_strips(L) * L.per_strip_bytes;
+    return default_exec_bytes(L);
 }
 
 extern "C" pcmm_status pcmm_cussen_execute(const void* plan, int m, int n, int w, int k,
@@ -225,11 +303,11 @@ extern "C" pcmm_status pcmm_cussen_execute(const void* plan, int m, int n, int w
         return PCMM_EINVAL;
     Layout L;
     if (!make_layout(L, m, n, l, w, k)) return PCMM_EINVAL;
-    if (ws_bytes < L.per_strip_bytes) return PCMM_ENOMEM;
-    size_t S = ws_bytes / L.per_strip_bytes;
-    if (S > (size_t)L.nstrips) S = L.nstrips;
-    return launch_exec(L, plan_ptrs(L, const_cast<void*>(plan)), ctB, ctC, (uint8_t*)ws, S,
-                       (cudaStream_t)stream);
+    size_t S, pbytes;
+    int parts;
+    if (!exec_space(L, ws_bytes, S, parts, pbytes)) return PCMM_ENOMEM;
+    return launch_exec(L, plan_ptrs(L, const_cast<void*>(plan)), ctB, ctC, (uint8_t*)ws + pbytes, S,
+                       (uint8_t*)ws, parts, (cudaStream_t)stream);
 }
 
 extern "C" pcmm_status pcmm_workspace_status(const void* ws, uint32_t* status_host, pcmm_stream_t stream) {

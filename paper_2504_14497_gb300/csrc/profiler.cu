@@ -18,7 +18,7 @@ std::vector<Slot> g_slots;
 int g_used = 0;
 bool g_on = false;
 const char* const g_names[KID_COUNT] = {"plan", "table", "gather", "normalize",
-                                        "encrypt", "schoolbook", "comb", "batched"};
+                                        "encrypt", "schoolbook", "comb", "batched", "combine"};
 }  // namespace
 
 ProfScope::ProfScope(int kernel_id, cudaStream_t s) : slot(-1), stream(s) {

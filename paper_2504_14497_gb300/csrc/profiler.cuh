@@ -14,7 +14,8 @@ enum KernelId {
     KID_SCHOOLBOOK = 5,
     KID_COMB = 6,
     KID_BATCHED = 7,
-    KID_COUNT = 8
+    KID_COMBINE = 8,
+    KID_COUNT = 9
 };
 
 // Records a start event on construction and a stop event on destruction
