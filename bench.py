@@ -90,6 +90,13 @@ class Dist:
             self.pg.destroy_process_group()
 
 
+def replica_rate(world: int, units_per_rank: float, steps: int, max_ms: float) -> float:
+    """Whole-job throughput of `world` replicas that each processed
+    units_per_rank units per step for `steps` steps, timed by the slowest
+    rank (max_ms over ranks)."""
+    return world * units_per_rank * steps / (max_ms / 1e3)
+
+
 # ----------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -298,7 +305,7 @@ def run_ours(args, dist):
     total_ms = dist.max(total_ms)
 
     ops_step = sum(counts.point_ops(r["counts"]) for r in runs)
-    value = dist.world * ops_step * args.steps / (total_ms / 1e3)
+    value = replica_rate(dist.world, ops_step, args.steps, total_ms)
     launches = sum(v[1] for v in prof.values())
 
     # ---- roofline of the dominant kernel (integer multiply-add bound)
@@ -373,7 +380,7 @@ def run_ours(args, dist):
             ev1.synchronize()
             e2e_ms += ev0.elapsed_time(ev1)
         e2e_ms = dist.max(e2e_ms)
-        e2e = {"value": dist.world * ops_step * args.steps / (e2e_ms / 1e3), "unit": UNIT,
+        e2e = {"value": replica_rate(dist.world, ops_step, args.steps, e2e_ms), "unit": UNIT,
                "h2d_bytes_per_step": int(hB.numel() * 4 + sum(a.numel() for a in hA)),
                "d2h_bytes_per_step": int(sum(c.numel() * 4 for c in hC)),
                "ms_per_step": e2e_ms / args.steps}
