@@ -68,7 +68,13 @@ __global__ void __launch_bounds__(PLAN_THREADS) batched_plan_kernel(const Inst* 
     plan_strip(I.A, I.m, I.n, I.w, I.k, I.P, is.y);
 }
 
-__global__ void __launch_bounds__(BATCH_THREADS) batched_kernel(const Inst* __restrict__ insts,
+// Resident blocks per SM requested from the compiler: 4 (128 registers, some
+// spilled) measured 1256.9 ms for the 64-instance batch against 1497.9 ms
+// uncapped (168 registers, 3 blocks) and 1262.7 ms at 5 blocks.
+#ifndef PCMM_BATCH_MINBLOCKS
+#define PCMM_BATCH_MINBLOCKS 4
+#endif
+__global__ void __launch_bounds__(BATCH_THREADS, PCMM_BATCH_MINBLOCKS) batched_kernel(const Inst* __restrict__ insts,
                                                                 const Segment* __restrict__ segs, int nsegs,
                                                                 long long ntasks, BatchHeader* hdr,
                                                                 int* ctrs, uint4* scratch,
