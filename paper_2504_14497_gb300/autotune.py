@@ -2,7 +2,8 @@
 
 For a problem shape (m, n, l, w) it times ``pcmm_cussen`` on the device for
 the strip widths around the library's cost-model choice and keeps the
-fastest.  Inputs are synthetic (uniform w-bit A, random words for the ciphertext
+fastest (the cost model's choice unless another is at least 2% faster).
+Inputs are synthetic (uniform w-bit A, random words for the ciphertext
 coordinates): the kernels' work depends on the distinct values of A, not on
 the points.  Results are cached in a JSON file (``PCMM_AUTOTUNE_CACHE``
 or the path given) keyed by ``"m,n,l,w"``.
@@ -48,7 +49,8 @@ def _synthetic(m, n, l, w, device, seed=0):
     import torch
 
     rng = np.random.default_rng(seed)
-    A = torch.from_numpy(rng.integers(0, 1 << w, size=(m, n), dtype=np.uint8)).to(device)
+    A_host = rng.integers(0, 1 << w, size=(m, n), dtype=np.uint8 if w <= 8 else np.uint16)
+    A = pcmm.plaintext16(A_host, device) if w > 8 else torch.from_numpy(A_host).to(device)
     words = rng.integers(0, 1 << 32, size=(32 * n * l,), dtype=np.uint64).astype(np.uint32)
     ctB = pcmm.to_device_words(words, device)
     return A, ctB
@@ -78,7 +80,12 @@ def tune(m: int, n: int, l: int, w: int, device="cuda", reps: int = 2, cache=Non
             best = min(best, e0.elapsed_time(e1))
         times[k] = best
         del ws
+    # The cost model's choice stands unless another width is measurably
+    # (2%) faster, so that timing noise does not flip near-ties between runs.
+    k0 = pcmm.choose_k(m, n, l, w)
     k_best = min(times, key=times.get)
+    if k0 in times and times[k_best] > 0.98 * times[k0]:
+        k_best = k0
     cache[key] = {"k": int(k_best), "ms": {str(k): t for k, t in times.items()}}
     save_cache(cache, path)
     return int(k_best)
