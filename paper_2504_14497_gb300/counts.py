@@ -13,8 +13,10 @@ needs none), each product costing two IMAD instructions (low and high word):
     mixed addition    (madd-2007-bl, 7M + 4S)   592 products
     full addition     (add-2007-bl, 11M + 5S)   884 products
     doubling, a = -3  (dbl-2001-b, 3M + 5S)     372 products
-    normalisation of one table entry (3M for simultaneous inversion,
+    normalisation of one level-2 entry (3M for simultaneous inversion,
       then 1S + 3M for x = X Z^-2, y = Y Z^-3)  420 products
+    normalisation of one level-1 chain entry (Z^-1 walked backwards
+      along the chain's step ratios, 1M, then 1S + 3M)  292 products
     affine addition inside a batch (3M for the shared inversion, then
       1M + 1S + 1M for the slope, x3, y3)       356 products
 """
@@ -23,7 +25,7 @@ from __future__ import annotations
 import numpy as np
 
 N_ITER = 4
-PRODUCTS = {"madd": 592, "add": 884, "dbl": 372, "norm": 420, "affine": 356}
+PRODUCTS = {"madd": 592, "add": 884, "dbl": 372, "norm": 420, "norm_chain": 292, "affine": 356}
 IMAD_PER_PRODUCT = 2
 
 
@@ -47,14 +49,16 @@ def cussen_counts(A: np.ndarray, w: int, k: int, l: int, N: int = N_ITER) -> dic
     * ``table_madd``: level-1 prefix sums (Jacobian + affine);
     * ``table_affine``: k-tuple sums, affine additions sharing one inversion
       per round;
-    * ``table_norm``: entries normalised to affine (level 2, column tables when
-      k > 1, strip tables when k = 1);
+    * ``table_norm``: level-2 entries normalised to affine (simultaneous
+      inversion);
+    * ``table_norm_chain``: level-1 entries (the column tables when k > 1,
+      the strip tables when k = 1) normalised along their chain's ratios;
     * ``gather_madd``: accumulations of table entries into the outputs.
     Additions with an identity operand are copies and are not counted."""
     A = np.asarray(A).astype(np.int64) & ((1 << w) - 1)
     m, n = A.shape
     chains = 2 * l
-    tadd = tmadd = tdbl = tecsm = norm = taff = 0
+    tadd = tmadd = tdbl = tecsm = norm = nchain = taff = 0
     nnz_rows = np.zeros(m, dtype=np.int64)
     for s0 in range(0, n, k):
         cols = A[:, s0:s0 + k]
@@ -71,18 +75,19 @@ def cussen_counts(A: np.ndarray, w: int, k: int, l: int, N: int = N_ITER) -> dic
             tmadd += chains * max(lens[0] - 1, 0)
             norm += chains * (lens[1] if N > 1 else 0)
             if kw > 1:
-                norm += chains * lens[0]
+                nchain += chains * lens[0]
         distinct = np.unique(codes[codes != 0])
         if kw > 1:
             for code in distinct:
                 parts = sum(1 for t in range(kw) if (int(code) >> (w * t)) & ((1 << w) - 1))
                 taff += chains * max(parts - 1, 0)
         else:
-            norm += chains * len(distinct)
+            nchain += chains * len(distinct)
         nnz_rows += codes != 0
     gather = chains * int(np.maximum(nnz_rows - 1, 0).sum())
     return {"gather_madd": gather, "table_add": tadd, "table_madd": tmadd, "table_dbl": tdbl,
-            "table_ecsm_madd": tecsm, "table_norm": norm, "table_affine": taff}
+            "table_ecsm_madd": tecsm, "table_norm": norm, "table_norm_chain": nchain,
+            "table_affine": taff}
 
 
 def point_ops(c: dict) -> int:
@@ -99,6 +104,7 @@ def table_imad(c: dict) -> int:
     p = (c["table_add"] * PRODUCTS["add"]
          + (c["table_madd"] + c["table_ecsm_madd"]) * PRODUCTS["madd"]
          + c["table_dbl"] * PRODUCTS["dbl"] + c["table_norm"] * PRODUCTS["norm"]
+         + c["table_norm_chain"] * PRODUCTS["norm_chain"]
          + c["table_affine"] * PRODUCTS["affine"])
     return p * IMAD_PER_PRODUCT
 

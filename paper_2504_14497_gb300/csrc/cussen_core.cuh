@@ -523,6 +523,61 @@ __device__ __forceinline__ void lp_normalize(const uint4* src, int E, uint4* pre
     lp_normalize_back(src, E, pref, lane, acc, ones, store);
 }
 
+// Normalises the E entries of a chain P_e = P_{e-1} + Q_e (lane-planar
+// Jacobian in src) whose step ratios r_e = Z_e / Z_{e-1} were stored as
+// entry e of rat (jac_madd_ratio), so that Z_e = r_0 r_1 ... r_e and zlast =
+// Z_{E-1}: one warp-wide inversion of zlast, then going backwards Z_e^-1 is
+// in hand and Z_{e-1}^-1 = Z_e^-1 r_e, 4M + 1S per entry in all, and only
+// X, Y and r are read back.  Each lane's ok says whether its ratios are all
+// defined; if any lane's are not, the whole warp normalises the general way
+// (Montgomery's trick over the stored Z's, overwriting rat).  ones: every
+// ratio of this lane is 1 (so every Z is 1).  All 32 lanes call with the
+// same E.
+template <class Store>
+__device__ __forceinline__ void lp_normalize_ratio(const uint4* src, int E, uint4* rat, unsigned lane,
+                                                   const fe& zlast, bool ones, bool ok, Store store) {
+    if (E <= 0) return;
+    if (!__all_sync(0xffffffffu, ok)) {
+        lp_normalize(src, E, rat, lane, store);
+        return;
+    }
+    if (__all_sync(0xffffffffu, ones)) {
+        for (int e = 0; e < E; e++) {
+            jac Pe;
+            lp_load_jac(Pe, src, e, lane);
+            aff out;
+            fe_canon(out.x, Pe.X);
+            fe_canon(out.y, Pe.Y);
+            store(e, out);
+        }
+        return;
+    }
+    fe inv;
+    warp_inverse(inv, zlast);
+    for (int e = E - 1; e >= 0; e--) {
+        if (e >= 2) {
+            // lanes 0-15: the X and Y lines of entry e - 2; 16-23: its ratio.
+            const char* line = lane < 16u ? (const char*)(src + (size_t)(e - 2) * 192) + lane * 128u
+                                          : (lane < 24u ? (const char*)(rat + (size_t)(e - 2) * 64) +
+                                                              (lane - 16u) * 128u
+                                                        : nullptr);
+            if (line) asm volatile("prefetch.global.L2 [%0];" ::"l"(line));
+        }
+        const uint4* b = src + (size_t)e * 6 * 32 + lane;
+        jac Pe;
+        fe_from_quads(Pe.X, b[0], b[32]);
+        fe_from_quads(Pe.Y, b[64], b[96]);
+        aff out;
+        jac_to_aff_with_zinv(out, Pe, inv);
+        store(e, out);
+        if (e > 0) {
+            fe r;
+            lp_load_fe(r, rat, e, lane);
+            inv = fmul(inv, r);
+        }
+    }
+}
+
 // One warp per (strip, component c, 32 output columns); all lanes follow the
 // same plan, so the control flow is warp-uniform.
 // Table of one warp item (strip, component, 32 output columns) of a chunk;
@@ -603,29 +658,30 @@ __device__ __forceinline__ void table_item(const TableArgs& a, const PlanPtrs& P
         else lp_normalize(src, lens[1], pref, lane, store_l2);
         // Level 1: the multiples of the column's sorted distinct values,
         // with the forward pass of their normalisation.
-        fe cacc;
-        bool cones = true;
-        fe_one(cacc);
+        // The step ratios of the chain go to pref, for the normalisation.
+        jac acc;
+        bool cones = true, cok = true;
         {
             const uint16_t* ptr = col_level_ptr(P, col, 1);
-            jac acc;
             aff D;
             jac_set_inf(acc);
             for (int e = 0; e < lens[0]; e++) {
                 lp_load_aff(D, l2aff, ptr[e], lane);
-                jac_madd(acc, D);
+                fe r;
+                jac_madd_ratio(acc, D, r, cok, e == 0);
                 lp_store_jac(coltab, e, lane, acc);
-                lp_pref_step(cacc, cones, acc.Z, pref, e, lane);
+                cones &= fe_is_one(r);
+                lp_store_fe(pref, e, lane, r);
             }
         }
         if (a.k == 1) {
             // The column table is the strip table (E = lens[0] entries).
-            lp_normalize_back(coltab, E, pref, lane, cacc, cones, store_table);
+            lp_normalize_ratio(coltab, E, pref, lane, acc.Z, cones, cok, store_table);
             return;
         }
         uint4* ca = colaff + (size_t)t * a.n1max * 128;
-        lp_normalize_back(coltab, lens[0], pref, lane, cacc, cones,
-                          [&](int e, const aff& q) { lp_store_aff(ca, e, lane, q); });
+        lp_normalize_ratio(coltab, lens[0], pref, lane, acc.Z, cones, cok,
+                           [&](int e, const aff& q) { lp_store_aff(ca, e, lane, q); });
     }
     if (bad) {
         if (lane == 0) atomicOr(P.status, DEV_ERR_PLAN);
@@ -813,15 +869,16 @@ inline double expected_distinct_nonzero(int m, int bits) {
 // counted as one) for strip width k.  Gather: one mixed addition (11) per
 // row, strip and ciphertext chain with a non-zero code.  Table build: per
 // column the level-1 prefix sums (mixed additions) and the level-N
-// double-and-add (about 2w operations of 8); the normalisation (7 per entry)
-// of the strip table (k = 1) or of the column tables (k > 1); for k > 1 the
+// double-and-add (about 2w operations of 8); the normalisation (5 per entry,
+// along the chain's ratios) of the strip table (k = 1) or of the column
+// tables (k > 1); for k > 1 the
 // tuple entries by affine additions (6 per further non-zero component).  The
 // table work is weighted by 1.9, fitted to GB300 timings of the
 // 1024 x 1024 x 256 product for every w and k (the table build issues its
 // multiplications less efficiently than the gather, and its tuple rounds
 // reload their operands from scratch).
 inline double model_cost(int m, int n, int l, int w, int k) {
-    const double MADD = 11, DBL = 8, NORM = 7, AFF = 6, TABLE_WEIGHT = 1.9;
+    const double MADD = 11, DBL = 8, NORM = 5, AFF = 6, TABLE_WEIGHT = 1.9;
     const double chains = 2.0 * l;
     const int nstrips = (n + k - 1) / k;
     const double n1 = expected_distinct_nonzero(m, w);

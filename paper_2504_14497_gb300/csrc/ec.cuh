@@ -127,6 +127,57 @@ __device__ __forceinline__ void jac_madd(jac& P, const aff& Q) {
     P.X = x3;
 }
 
+// jac_madd for a chain of additions (P_e = P_{e-1} + Q_e) that is later
+// normalised by walking the inverse of Z backwards: also returns r with
+// Z3 = r Z1 (H for an addition, 2 Y1 for a doubling, 1 when Q is infinity;
+// for the first step, from infinity, Z3 = 1 and r = 1).  ok is cleared when
+// no such r exists (P at infinity after the first step, or a result at
+// infinity); the caller then normalises the chain the general way.
+__device__ __forceinline__ void jac_madd_ratio(jac& P, const aff& Q, fe& r, bool& ok, bool first) {
+    fe_one(r);
+    if (aff_is_inf(Q)) {
+        if (jac_is_inf(P)) ok = false;
+        return;
+    }
+    if (jac_is_inf(P)) {
+        P.X = Q.x;
+        P.Y = Q.y;
+        fe_one(P.Z);
+        if (!first) ok = false;
+        return;
+    }
+    fe t1, t2, t3, t4, x3;
+    t1 = fsqr(P.Z);                  // Z1^2
+    t2 = fmul(t1, P.Z);              // Z1^3
+    t1 = fmul(t1, Q.x);              // U2
+    t2 = fmul(t2, Q.y);              // S2
+    fe_sub(t1, t1, P.X);             // H
+    fe_sub(t2, t2, P.Y);             // R
+    if (fe_is_zero(t1)) {
+        if (fe_is_zero(t2)) {        // same point: Z3 = 2 Y1 Z1
+            fe_add(r, P.Y, P.Y);
+            jac_dbl(P);
+            if (fe_is_zero(r) || jac_is_inf(P)) ok = false;
+        } else {                     // opposite points
+            jac_set_inf(P);
+            ok = false;
+        }
+        return;
+    }
+    r = t1;
+    P.Z = fmul(P.Z, t1);             // Z3 = Z1 H
+    t4 = fsqr(t1);                   // H^2
+    t3 = fmul(t4, t1);               // H^3
+    t4 = fmul(t4, P.X);              // X1 H^2
+    fe_add(t1, t4, t4);              // 2 X1 H^2
+    x3 = fsqr(t2);                   // R^2
+    fe_sub(x3, x3, t1);
+    fe_sub(x3, x3, t3);              // X3 = R^2 - 2 X1 H^2 - H^3
+    fe_sub(t4, t4, x3);              // X1 H^2 - X3
+    P.Y = fmulsub(t4, t2, t3, P.Y);  // Y3 = R (X1 H^2 - X3) - Y1 H^3
+    P.X = x3;
+}
+
 // P <- P + Q, both Jacobian, complete.
 __device__ __forceinline__ void jac_add(jac& P, const jac& Q) {
     if (jac_is_inf(Q)) return;
