@@ -48,12 +48,16 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-schoolbook", action="store_true")
-    ap.add_argument("--workload", choices=["large", "serving", "batched", "sweep"], default="large",
+    ap.add_argument("--workload", choices=["large", "serving", "batched", "sweep", "vector"], default="large",
                     help="large: the single large PC-MM (the headline line); serving: Poisson "
                          "request sweep of encrypted linear layers; batched: 64 uneven instances; "
-                         "sweep: square PC-MM over n and w, Cussen beside schoolbook")
+                         "sweep: square PC-MM over n and w, Cussen beside schoolbook; vector: "
+                         "plaintext vector times ciphertext scalars")
     ap.add_argument("--sweep-n", default="128,256,512,1024,2048")
     ap.add_argument("--sweep-widths", default="1,2,3,4,5,6,7,8,12,16")
+    ap.add_argument("--vector-n", default="8,16,32,64,128,256,512")
+    ap.add_argument("--vector-widths", default="4,8,12,16")
+    ap.add_argument("--vector-scalars", type=int, default=65536)
     ap.add_argument("--rates", default="10,20,50,100,200,500,1000,2000")
     ap.add_argument("--seconds", type=float, default=2.0, help="arrival window per rate (serving)")
     return ap.parse_args()
@@ -570,6 +574,70 @@ def run_sweep(args, dist):
             "peak_imad_per_s": peak, "clocks": clk, "rows": rows, "n_gpus": 1, "data": "synthetic (seeded)"}
 
 
+def run_vector(args, dist):
+    """Plaintext vector times ciphertext scalar (the paper's Sections 3.2 and
+    4.2): a vector a of n t-bit entries times one ciphertext, giving n
+    ciphertexts a_i Enc(b).  L products with independent ciphertext scalars
+    and the same vector run as one PC-MM with A = a (n x 1) and Enc(B) 1 x L;
+    the compression of a is shared, the table build of each scalar is the
+    vector-scalar product.  Reports the device time per product (Cussen and
+    schoolbook) and the point additions per second."""
+    import torch
+
+    from paper_2504_14497_gb300 import build, counts, inputs, pcmm
+
+    build.build()
+    torch.cuda.set_device(dist.local)
+    dev = torch.device("cuda", dist.local)
+    pcmm.init(dist.local)
+    seed = 2504144970 + 6
+    L = int(args.vector_scalars)
+    pr = inputs.pcmm_problem(seed, 1, 1, L, 1)
+    tab = pcmm.keytable(pcmm.public_key(pr["sk"], device=dev), device=dev)
+    ctB = pcmm.encrypt(tab, torch.from_numpy(pr["B"].reshape(-1)).to(dev),
+                       pcmm.to_device_words(pcmm.scalars_to_planar(pr["r"]), dev))
+    cur = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(cur)
+            fn()
+            e1.record(cur)
+            e1.synchronize()
+            t = e0.elapsed_time(e1)
+            best = t if best is None else min(best, t)
+        return best
+
+    rows = []
+    for nv in (int(x) for x in args.vector_n.split(",")):
+        out = torch.empty(48 * nv * L, dtype=torch.int32, device=dev)
+        for w in (int(x) for x in args.vector_widths.split(",")):
+            a_h = inputs.plaintext_matrix(seed, nv, 1, w)
+            A = _host_plaintext(a_h).to(dev)
+            ws = pcmm.workspace(nv, 1, L, w, 1, device=dev)
+            ms = timed(lambda: pcmm.cussen(A, ctB, L, w, k=1, ws=ws, out=out))
+            if pcmm.workspace_status(ws) != 0:
+                raise RuntimeError(f"device status at n={nv} w={w}")
+            del ws
+            sb = timed(lambda: pcmm.schoolbook(A, ctB, L, w, out=out))
+            ops = counts.point_ops(counts.cussen_counts(a_h, w, 1, L))
+            rows.append({"n": nv, "t": w, "cussen_us_per_product": 1e3 * ms / L,
+                         "schoolbook_us_per_product": 1e3 * sb / L, "speedup_vs_schoolbook": sb / ms,
+                         "point_adds_per_s": ops / (ms / 1e3)})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+            torch.cuda.empty_cache()
+        del out
+        torch.cuda.empty_cache()
+    return {"workload": f"vector x ciphertext scalar: a (n, t-bit) times {L} independent ciphertext scalars "
+                        "as one PC-MM (A n x 1, Enc(B) 1 x L), 8-bit messages",
+            "metric": "device time per vector-scalar product", "unit": "us", "scalars": L,
+            "rows": rows, "n_gpus": 1, "data": "synthetic (seeded)"}
+
+
 SERVING_MODELS = {"mlp_784": (256, 784), "mlp_256": (128, 256), "mlp_out": (10, 128)}
 
 
@@ -674,6 +742,8 @@ def main():
             out = run_batched(args, dist)
         elif args.workload == "sweep":
             out = run_sweep(args, dist)
+        elif args.workload == "vector":
+            out = run_vector(args, dist)
         else:
             out = run_ours(args, dist)
         if dist.rank == 0 and out is not None:

@@ -164,6 +164,24 @@ def test_chunked_passes_match_single_pass(dev):
     assert passes >= 4
 
 
+def test_split_gather_over_several_passes(dev):
+    # 16 rows x 8 columns give only 32 gather warps, so every output's strips
+    # are split over several warps (partial sums added by the combine
+    # kernel); smaller workspaces add passes, so the combine also adds onto
+    # the previous passes' sums.  Workspaces too small for the partial sums
+    # fall back to an unsplit gather.
+    m, n, l, w = 16, 200, 8, 4
+    pr, A, ctB = _problem(dev, 820, m, n, l, w)
+    want = _want(pr)
+    full = pcmm.workspace_bytes(m, n, l, w, 1)
+    plan = pcmm.lib().pcmm_cussen_plan_bytes(m, n, w, 1)
+    for nb in (full, plan + (full - plan) // 3, plan + (full - plan) // 7, plan + (full - plan) // 40):
+        ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+        got = run_affine(lambda: pcmm.cussen(A, ctB, l, w, k=1, ws=ws), m * l)
+        assert pcmm.workspace_status(ws) == 0
+        assert mismatches(got, want) == 0, nb
+
+
 def test_workspace_too_small_and_bad_arguments(dev):
     m, n, l, w = 8, 8, 8, 4
     pr, A, ctB = _problem(dev, 900, m, n, l, w)

@@ -162,3 +162,21 @@ def test_wide_maximum_rows(dev):
     pairs = np.stack([rows, np.zeros_like(rows)], axis=1)
     want = oracle.closed_form(pr["A"], pr["r"], pr["sk"], pr["B"], pairs=pairs)
     assert mismatches(got[rows], want) == 0
+
+
+@pytest.mark.parametrize("w", [4, 16])
+def test_vector_times_ciphertext_scalars(dev, w):
+    # The paper's plaintext-vector x ciphertext-scalar product: A is one
+    # column (n = 1), Enc(B) a row of independent scalars, as bench.py's
+    # vector workload runs it.
+    m, n, l = 512, 1, 200
+    pr = inputs.pcmm_problem(2100 + w, m, n, l, w)
+    ctB = encrypt_gpu(dev, pr)
+    A = pcmm.plaintext16(pr["A"], dev) if w > 8 else torch.from_numpy(pr["A"]).to(dev)
+    for fn in (lambda: pcmm.cussen(A, ctB, l, w, k=1), lambda: pcmm.schoolbook(A, ctB, l, w)):
+        got = run_affine(fn, m * l)
+        rng = np.random.default_rng(w)
+        pairs = np.stack([rng.integers(0, m, 80), rng.integers(0, l, 80)], axis=1)
+        pairs = np.concatenate([pairs, [[0, 0], [m - 1, l - 1]]])
+        want = oracle.closed_form(pr["A"], pr["r"], pr["sk"], pr["B"], pairs=pairs)
+        assert mismatches(got[pairs[:, 0] * l + pairs[:, 1]], want) == 0
