@@ -276,7 +276,8 @@ pcmm_status pcmm_batched_run(const pcmm_batch_info *info, void *ws, pcmm_stream_
 pcmm_status pcmm_workspace_status(const void *ws, uint32_t *status_host, pcmm_stream_t stream);
 
 /* Normalises a Jacobian ciphertext array to canonical affine form
- * (Montgomery's simultaneous inversion, one field inversion per 64 points).
+ * (Montgomery's simultaneous inversion: each thread takes up to 8
+ * ciphertexts, one field inversion per warp, so per 64 to 512 points).
  * ct_jac: device, 48 * count words; ct_aff: device, 32 * count words
  * (may not overlap).  Errors: PCMM_EINVAL, PCMM_ECUDA. */
 pcmm_status pcmm_normalize(const uint32_t *ct_jac, size_t count, uint32_t *ct_aff,

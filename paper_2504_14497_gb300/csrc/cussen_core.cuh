@@ -432,10 +432,6 @@ __device__ __forceinline__ void lp_load_aff(aff& Q, const uint4* base, int e, un
     fe_from_quads(Q.y, b[64], b[96]);
 }
 
-__device__ __forceinline__ bool fe_is_one(const fe& a) {
-    uint32_t z = (a.v[0] ^ 1u) | a.v[1] | a.v[2] | a.v[3] | a.v[4] | a.v[5] | a.v[6] | a.v[7];
-    return z == 0u;
-}
 
 // One forward step of the simultaneous inversion, for loops that produce
 // lane-planar Jacobian entries: acc *= Z_e (a zero Z, i.e. infinity, counts

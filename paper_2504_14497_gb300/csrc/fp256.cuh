@@ -170,6 +170,14 @@ __device__ __forceinline__ bool fe_equal(const fe& a, const fe& b) {
     return fe_is_zero(d);
 }
 
+// Whether a holds exactly the word representation of 1 (a value of 1 + p,
+// which weakly reduced arithmetic could produce, is not recognised; callers
+// use this only to skip work when it says yes).
+__device__ __forceinline__ bool fe_is_one(const fe& a) {
+    uint32_t z = (a.v[0] ^ 1u) | a.v[1] | a.v[2] | a.v[3] | a.v[4] | a.v[5] | a.v[6] | a.v[7];
+    return z == 0u;
+}
+
 // Reduce the 512-bit value c[0..15] modulo p into r (weak).
 __device__ __forceinline__ void fe_reduce(fe& r, const uint32_t c[16]) {
     uint32_t a0, a1, a2, a3, a4, a5, a6, a7, a8;
