@@ -83,6 +83,71 @@ __device__ __forceinline__ void warp_inverse(fe& tinv, const fe& t) {
     tinv = fmul(inv, sex);
 }
 
+// warp_inverse with one field inversion shared by the four warps of a
+// 128-thread block (the inversion, executed by every lane of a warp, costs
+// as much as about 250 multiplications): each warp's total goes to shared
+// memory, warp 0 inverts the product of the four and hands each warp the
+// inverse of its total.  All 128 threads of the block must call, in the same
+// order as every other block-level call (blockDim.x must be 128).
+static __device__ __noinline__ fe block4_inverse(fe t) {
+    __shared__ fe sh_tot[4];
+    __shared__ fe sh_inv[4];
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    fe pre = t, suf = t, o;
+#pragma unroll
+    for (unsigned d = 1; d < 32; d <<= 1) {
+        o = fe_shfl_up(pre, d);
+        if (lane >= d) pre = fmul(pre, o);
+    }
+#pragma unroll
+    for (unsigned d = 1; d < 32; d <<= 1) {
+        o = fe_shfl_down(suf, d);
+        if (lane + d < 32u) suf = fmul(suf, o);
+    }
+    fe total = fe_shfl(pre, 31);
+    fe pex = fe_shfl_up(pre, 1);
+    fe sex = fe_shfl_down(suf, 1);
+    if (lane == 0) fe_one(pex);
+    if (lane == 31) fe_one(sex);
+    if (lane == 0) sh_tot[warp] = total;
+    __syncthreads();
+    if (warp == 0) {
+        const fe p01 = fmul(sh_tot[0], sh_tot[1]);
+        const fe p012 = fmul(p01, sh_tot[2]);
+        fe i;
+        fe_inv(i, fmul(p012, sh_tot[3]));
+        const fe i3 = fmul(i, p012);                 // total_3^-1
+        const fe i012 = fmul(i, sh_tot[3]);          // (t0 t1 t2)^-1
+        const fe i2 = fmul(i012, p01);               // total_2^-1
+        const fe i01 = fmul(i012, sh_tot[2]);        // (t0 t1)^-1
+        const fe i1 = fmul(i01, sh_tot[0]);
+        const fe i0 = fmul(i01, sh_tot[1]);
+        if (lane == 0) {
+            sh_inv[0] = i0;
+            sh_inv[1] = i1;
+            sh_inv[2] = i2;
+            sh_inv[3] = i3;
+        }
+    }
+    __syncthreads();
+    fe inv = sh_inv[warp];
+    inv = fmul(inv, pex);
+    return fmul(inv, sex);
+}
+
+// t^-1 per lane: block4_inverse when `shared` (then all 128 threads of the
+// block must call), warp_inverse otherwise.
+__device__ __forceinline__ void group_inverse(fe& tinv, const fe& t, bool shared) {
+    if (shared) tinv = block4_inverse(t);
+    else warp_inverse(tinv, t);
+}
+
+// Whether x holds on every lane of the warp or, with `shared`, on every
+// thread of the block (then all threads of the block must call).
+__device__ __forceinline__ bool group_all(bool x, bool shared) {
+    return shared ? __syncthreads_and(x) != 0 : __all_sync(0xffffffffu, x);
+}
+
 // Normalise E Jacobian points held in each lane's registers to canonical
 // affine coordinates; infinity (Z = 0) becomes (0, 0).  One inversion per
 // warp for 32 * E points.  All 32 lanes must call.

@@ -416,6 +416,7 @@ struct TableArgs {
     size_t item_u4;
     uint4* table;          // affine, quad-planar, table_points points
     size_t table_points;
+    bool bshare;           // the 4 warps of each block share one strip's plan: share inversions
 };
 
 __device__ __forceinline__ void lp_store_aff(uint4* base, int e, unsigned lane, const aff& Q) {
@@ -456,9 +457,9 @@ __device__ __forceinline__ void lp_pref_step(fe& acc, bool& ones, const fe& Z, u
 // lanes call with the same E.
 template <class Store>
 __device__ __forceinline__ void lp_normalize_back(const uint4* src, int E, const uint4* pref, unsigned lane,
-                                                  fe acc, bool ones, Store store) {
+                                                  fe acc, bool ones, Store store, bool shared) {
     if (E <= 0) return;
-    if (__all_sync(0xffffffffu, ones)) {
+    if (group_all(ones, shared)) {
         for (int e = 0; e < E; e++) {
             jac Pe;
             lp_load_jac(Pe, src, e, lane);
@@ -470,7 +471,7 @@ __device__ __forceinline__ void lp_normalize_back(const uint4* src, int E, const
         return;
     }
     fe inv;
-    warp_inverse(inv, acc);
+    group_inverse(inv, acc, shared);
     for (int e = E - 1; e >= 0; e--) {
         if (e >= 2) {
             const char* line = lane < 24u ? (const char*)(src + (size_t)(e - 2) * 192) + lane * 128u
@@ -506,7 +507,7 @@ __device__ __forceinline__ void lp_normalize_back(const uint4* src, int E, const
 // Normalises E lane-planar Jacobian entries already in scratch (both passes).
 template <class Store>
 __device__ __forceinline__ void lp_normalize(const uint4* src, int E, uint4* pref, unsigned lane,
-                                             Store store) {
+                                             Store store, bool shared) {
     if (E <= 0) return;
     bool ones = true;
     fe acc;
@@ -516,7 +517,7 @@ __device__ __forceinline__ void lp_normalize(const uint4* src, int E, uint4* pre
         lp_load_z(z, src, e, lane);
         lp_pref_step(acc, ones, z, pref, e, lane);
     }
-    lp_normalize_back(src, E, pref, lane, acc, ones, store);
+    lp_normalize_back(src, E, pref, lane, acc, ones, store, shared);
 }
 
 // Normalises the E entries of a chain P_e = P_{e-1} + Q_e (lane-planar
@@ -531,13 +532,14 @@ __device__ __forceinline__ void lp_normalize(const uint4* src, int E, uint4* pre
 // same E.
 template <class Store>
 __device__ __forceinline__ void lp_normalize_ratio(const uint4* src, int E, uint4* rat, unsigned lane,
-                                                   const fe& zlast, bool ones, bool ok, Store store) {
+                                                   const fe& zlast, bool ones, bool ok, Store store,
+                                                   bool shared) {
     if (E <= 0) return;
-    if (!__all_sync(0xffffffffu, ok)) {
-        lp_normalize(src, E, rat, lane, store);
+    if (!group_all(ok, shared)) {
+        lp_normalize(src, E, rat, lane, store, shared);
         return;
     }
-    if (__all_sync(0xffffffffu, ones)) {
+    if (group_all(ones, shared)) {
         for (int e = 0; e < E; e++) {
             jac Pe;
             lp_load_jac(Pe, src, e, lane);
@@ -549,7 +551,7 @@ __device__ __forceinline__ void lp_normalize_ratio(const uint4* src, int E, uint
         return;
     }
     fe inv;
-    warp_inverse(inv, zlast);
+    group_inverse(inv, zlast, shared);
     for (int e = E - 1; e >= 0; e--) {
         if (e >= 2) {
             // lanes 0-15: the X and Y lines of entry e - 2; 16-23: its ratio.
@@ -650,8 +652,8 @@ __device__ __forceinline__ void table_item(const TableArgs& a, const PlanPtrs& P
         // Level 2 (multiples of the level-1 differences) to affine, so that
         // the level-1 prefix sums are mixed additions.
         auto store_l2 = [&](int e, const aff& q) { lp_store_aff(l2aff, e, lane, q); };
-        if (NLEV > 2) lp_normalize_back(src, lens[1], pref, lane, pacc, pones, store_l2);
-        else lp_normalize(src, lens[1], pref, lane, store_l2);
+        if (NLEV > 2) lp_normalize_back(src, lens[1], pref, lane, pacc, pones, store_l2, a.bshare);
+        else lp_normalize(src, lens[1], pref, lane, store_l2, a.bshare);
         // Level 1: the multiples of the column's sorted distinct values,
         // with the forward pass of their normalisation.
         // The step ratios of the chain go to pref, for the normalisation.
@@ -672,12 +674,12 @@ __device__ __forceinline__ void table_item(const TableArgs& a, const PlanPtrs& P
         }
         if (a.k == 1) {
             // The column table is the strip table (E = lens[0] entries).
-            lp_normalize_ratio(coltab, E, pref, lane, acc.Z, cones, cok, store_table);
+            lp_normalize_ratio(coltab, E, pref, lane, acc.Z, cones, cok, store_table, a.bshare);
             return;
         }
         uint4* ca = colaff + (size_t)t * a.n1max * 128;
         lp_normalize_ratio(coltab, lens[0], pref, lane, acc.Z, cones, cok,
-                           [&](int e, const aff& q) { lp_store_aff(ca, e, lane, q); });
+                           [&](int e, const aff& q) { lp_store_aff(ca, e, lane, q); }, a.bshare);
     }
     if (bad) {
         if (lane == 0) atomicOr(P.status, DEV_ERR_PLAN);
@@ -737,7 +739,7 @@ __device__ __forceinline__ void table_item(const TableArgs& a, const PlanPtrs& P
             lp_store_fe(pref, e, lane, acc);
         }
         fe inv;
-        warp_inverse(inv, acc);
+        group_inverse(inv, acc, a.bshare);
         for (int e = E - 1; e >= 0; e--) {
             const uint32_t code = P.codes[(size_t)s * a.emax + e];
             uint32_t vq, v0;

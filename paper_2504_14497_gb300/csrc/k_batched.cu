@@ -108,6 +108,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, PCMM_BATCH_MINBLOCKS) batched_k
             if (!__shfl_sync(0xffffffffu, ok, 0)) break;
             TableArgs ta;
             ta.ctB = I.ctB;
+            ta.bshare = false;       // warps take tasks independently
             ta.m = I.m; ta.n = I.n; ta.l = I.l; ta.w = I.w; ta.k = I.k;
             ta.lp = I.lp; ta.njb = I.njb; ta.n1max = I.n1max; ta.l2max = I.l2max; ta.emax = I.emax;
             ta.s0 = s0; ta.nstrips_chunk = sc;

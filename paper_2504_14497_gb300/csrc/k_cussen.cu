@@ -164,6 +164,10 @@ pcmm_status launch_exec(const Layout& L, const PlanPtrs& P, const uint32_t* ctB,
         ta.item_u4 = L.item_u4;
         ta.table = table;
         ta.table_points = S * L.table_points_per_strip;
+        // Four consecutive items (one 128-thread block) belong to one strip
+        // exactly when a strip has a multiple of 4 items; then every block is
+        // full and its warps follow the same plan, and share inversions.
+        ta.bshare = (L.items_per_strip % 4) == 0;
         const long long items = (long long)sc * L.items_per_strip;
         {
             ProfScope ps(KID_TABLE, st);
