@@ -11,6 +11,8 @@ Per-operation integer work, in 32x32->64-bit limb products (a field
 multiplication is 64 products, a squaring 36; P-256 special-form reduction
 needs none), each product costing two IMAD instructions (low and high word):
     mixed addition    (madd-2007-bl, 7M + 4S)   592 products
+    mixed addition into a gather accumulator kept as (X, Y, Z^2, Z^3)
+      (8M + 2S: Z^2 and Z^3 updated with H^2 and H^3)  584 products
     full addition     (add-2007-bl, 11M + 5S)   884 products
     doubling, a = -3  (dbl-2001-b, 3M + 5S)     372 products
     normalisation of one level-2 entry (3M for simultaneous inversion,
@@ -25,7 +27,8 @@ from __future__ import annotations
 import numpy as np
 
 N_ITER = 4
-PRODUCTS = {"madd": 592, "add": 884, "dbl": 372, "norm": 420, "norm_chain": 292, "affine": 356}
+PRODUCTS = {"madd": 592, "madd_acc": 584, "add": 884, "dbl": 372, "norm": 420, "norm_chain": 292,
+            "affine": 356}
 IMAD_PER_PRODUCT = 2
 
 
@@ -97,7 +100,7 @@ def point_ops(c: dict) -> int:
 
 
 def gather_imad(c: dict) -> int:
-    return c["gather_madd"] * PRODUCTS["madd"] * IMAD_PER_PRODUCT
+    return c["gather_madd"] * PRODUCTS["madd_acc"] * IMAD_PER_PRODUCT
 
 
 def table_imad(c: dict) -> int:

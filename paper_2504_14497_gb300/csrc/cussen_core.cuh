@@ -834,10 +834,17 @@ __device__ __forceinline__ void gather_item(const GatherArgs& a, const PlanPtrs&
     const int j = jb * 32 + (int)lane;
     const size_t ml = (size_t)a.m * a.l;
     uint4* Cc = (a.parts > 1 ? a.partial + (size_t)part * 12 * ml : a.ctC) + (size_t)c * 6 * ml;
-    jac acc;
-    if (a.first || a.parts > 1 || j >= a.l) jac_set_inf(acc);
-    else if (CG) load_jac_cg(acc, Cc, ml, (size_t)i * a.l + j);
-    else load_jac(acc, Cc, ml, (size_t)i * a.l + j);
+    // The running sum is kept as (X, Y, Z^2, Z^3): its mixed additions then
+    // cost 8M + 2S, and Z itself is rebuilt once at the end.
+    jacz acc;
+    if (a.first || a.parts > 1 || j >= a.l) {
+        jacz_set_inf(acc);
+    } else {
+        jac prev;
+        if (CG) load_jac_cg(prev, Cc, ml, (size_t)i * a.l + j);
+        else load_jac(prev, Cc, ml, (size_t)i * a.l + j);
+        jacz_from_jac(acc, prev);
+    }
     const uint16_t* rk = P.rank + (size_t)a.s0 * a.m + i;
     aff T;
     const int s_lo = (int)((long long)a.nstrips_chunk * part / a.parts);
@@ -848,9 +855,13 @@ __device__ __forceinline__ void gather_item(const GatherArgs& a, const PlanPtrs&
         const size_t ti = (((size_t)sl * a.emax + code) * 2 + c) * a.lp + j;
         if (CG) load_aff_cg(T, a.table, a.table_points, ti);
         else load_aff(T, a.table, a.table_points, ti);
-        jac_madd(acc, T);
+        jacz_madd(acc, T);
     }
-    if (j < a.l) store_jac(Cc, ml, (size_t)i * a.l + j, acc);
+    if (j < a.l) {
+        jac out;
+        jac_from_jacz(out, acc);
+        store_jac(Cc, ml, (size_t)i * a.l + j, out);
+    }
 }
 
 // Expected number of distinct non-zero values when m values are drawn

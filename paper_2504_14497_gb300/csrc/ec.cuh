@@ -178,6 +178,80 @@ __device__ __forceinline__ void jac_madd_ratio(jac& P, const aff& Q, fe& r, bool
     P.X = x3;
 }
 
+// Accumulator of a long run of mixed additions in which Z is never needed
+// itself: (X, Y, ZZ, ZZZ) with ZZ = Z^2 and ZZZ = Z^3 of some Jacobian Z
+// (infinity: ZZ = ZZZ = 0).  A mixed addition then updates ZZ and ZZZ with
+// the H^2 and H^3 it computes anyway (8M + 2S instead of 8M + 3S).
+struct jacz {
+    fe X, Y, ZZ, ZZZ;
+};
+
+__device__ __forceinline__ void jacz_set_inf(jacz& P) {
+    fe_one(P.X);
+    fe_one(P.Y);
+    fe_zero(P.ZZ);
+    fe_zero(P.ZZZ);
+}
+
+__device__ __forceinline__ void jacz_from_jac(jacz& R, const jac& P) {
+    R.X = P.X;
+    R.Y = P.Y;
+    R.ZZ = fsqr(P.Z);
+    R.ZZZ = fmul(R.ZZ, P.Z);
+}
+
+// Jacobian representative without an inversion: with Z' = ZZ ZZZ = Z^5,
+// X' = x Z'^2 = X ZZ^4 and Y' = y Z'^3 = Y ZZZ^4 (4S + 3M).  Infinity maps
+// to Z' = 0.
+__device__ __forceinline__ void jac_from_jacz(jac& R, const jacz& P) {
+    fe t = fsqr(P.ZZ);
+    t = fsqr(t);
+    R.X = fmul(P.X, t);
+    t = fsqr(P.ZZZ);
+    t = fsqr(t);
+    R.Y = fmul(P.Y, t);
+    R.Z = fmul(P.ZZ, P.ZZZ);
+}
+
+__device__ __forceinline__ void jacz_madd(jacz& P, const aff& Q) {
+    if (aff_is_inf(Q)) return;
+    if (fe_is_zero(P.ZZ)) {
+        P.X = Q.x;
+        P.Y = Q.y;
+        fe_one(P.ZZ);
+        fe_one(P.ZZZ);
+        return;
+    }
+    fe t1, t2, t3, t4, x3;
+    t1 = fmul(P.ZZ, Q.x);            // U2
+    t2 = fmul(P.ZZZ, Q.y);           // S2
+    fe_sub(t1, t1, P.X);             // H
+    fe_sub(t2, t2, P.Y);             // R
+    if (fe_is_zero(t1)) {
+        if (fe_is_zero(t2)) {        // P = Q: the result is 2Q, from Q's affine coordinates
+            jac D;
+            jac_from_aff(D, Q);
+            jac_dbl(D);
+            jacz_from_jac(P, D);
+        } else {                     // P = -Q
+            jacz_set_inf(P);
+        }
+        return;
+    }
+    t4 = fsqr(t1);                   // H^2
+    t3 = fmul(t4, t1);               // H^3
+    P.ZZ = fmul(P.ZZ, t4);           // ZZ3 = ZZ1 H^2
+    P.ZZZ = fmul(P.ZZZ, t3);         // ZZZ3 = ZZZ1 H^3
+    t4 = fmul(t4, P.X);              // X1 H^2
+    fe_add(t1, t4, t4);              // 2 X1 H^2
+    x3 = fsqr(t2);                   // R^2
+    fe_sub(x3, x3, t1);
+    fe_sub(x3, x3, t3);              // X3 = R^2 - 2 X1 H^2 - H^3
+    fe_sub(t4, t4, x3);              // X1 H^2 - X3
+    P.Y = fmulsub(t4, t2, t3, P.Y);  // Y3 = R (X1 H^2 - X3) - Y1 H^3
+    P.X = x3;
+}
+
 // P <- P + Q, both Jacobian, complete.
 __device__ __forceinline__ void jac_add(jac& P, const jac& Q) {
     if (jac_is_inf(Q)) return;

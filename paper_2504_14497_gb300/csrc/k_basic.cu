@@ -115,9 +115,9 @@ __global__ void __launch_bounds__(128) base_mul_kernel(const uint4* __restrict__
 // Jacobian ciphertexts -> canonical affine.  Thread t takes the G
 // ciphertexts i = g T + t (T threads in the grid, g < G; each g is a
 // coalesced sweep), that is 2G points, and the warp shares one field
-// inversion among its 64 G points (Montgomery's simultaneous inversion,
-// prefix products across each lane's points, then across the warp by
-// shuffles).  The prefix products wait in the output's x words, which the
+// inversion among its 64 G points, and the four warps of the block share
+// one (Montgomery's simultaneous inversion: prefix products across each
+// lane's points, across the warp by shuffles, across the block's warps).  The prefix products wait in the output's x words, which the
 // backward pass overwrites point by point after reading them.
 __global__ void __launch_bounds__(128) normalize_kernel(const uint4* __restrict__ in, size_t count,
                                                         uint4* __restrict__ out, int G) {
@@ -143,7 +143,9 @@ __global__ void __launch_bounds__(128) normalize_kernel(const uint4* __restrict_
             o[count + i] = fe_hi(acc);
         }
     }
-    if (__all_sync(0xffffffffu, ones)) {
+    // Every thread of the (128-thread) block reaches this point, with or
+    // without ciphertexts, so the block votes and shares one inversion.
+    if (group_all(ones, true)) {
         for (int g = 0; g < G; g++) {
             const size_t i = (size_t)g * T + t;
             if (i >= count) break;
@@ -160,7 +162,7 @@ __global__ void __launch_bounds__(128) normalize_kernel(const uint4* __restrict_
         return;
     }
     fe inv;
-    warp_inverse(inv, acc);
+    group_inverse(inv, acc, true);
     for (int g = G - 1; g >= 0; g--) {
         const size_t i = (size_t)g * T + t;
         if (i >= count) continue;
