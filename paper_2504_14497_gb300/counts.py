@@ -11,14 +11,15 @@ Per-operation integer work, in 32x32->64-bit limb products (a field
 multiplication is 64 products, a squaring 36; P-256 special-form reduction
 needs none), each product costing two IMAD instructions (low and high word):
     mixed addition    (madd-2007-bl, 7M + 4S)   592 products
-    mixed addition into a gather accumulator kept as (X, Y, Z^2, Z^3)
-      (8M + 2S: Z^2 and Z^3 updated with H^2 and H^3)  584 products
+    mixed addition into an accumulator kept as (X, Y, Z^2, Z^3) (gather,
+      level-1 chains; 8M + 2S: Z^2 and Z^3 updated with H^2 and H^3)  584 products
     full addition     (add-2007-bl, 11M + 5S)   884 products
     doubling, a = -3  (dbl-2001-b, 3M + 5S)     372 products
     normalisation of one level-2 entry (3M for simultaneous inversion,
       then 1S + 3M for x = X Z^-2, y = Y Z^-3)  420 products
-    normalisation of one level-1 chain entry (Z^-1 walked backwards
-      along the chain's step ratios, 1M, then 1S + 3M)  292 products
+    normalisation of one level-1 chain entry (the chain kept as (X, Y,
+      Z^2, Z^3); Z^-2 and Z^-3 walked backwards along the chain's factors
+      H^2, H^3, 2M, then x = X Z^-2, y = Y Z^-3, 2M)  256 products
     affine addition inside a batch (3M for the shared inversion, then
       1M + 1S + 1M for the slope, x3, y3)       356 products
 """
@@ -27,7 +28,7 @@ from __future__ import annotations
 import numpy as np
 
 N_ITER = 4
-PRODUCTS = {"madd": 592, "madd_acc": 584, "add": 884, "dbl": 372, "norm": 420, "norm_chain": 292,
+PRODUCTS = {"madd": 592, "madd_acc": 584, "add": 884, "dbl": 372, "norm": 420, "norm_chain": 256,
             "affine": 356}
 IMAD_PER_PRODUCT = 2
 
@@ -105,7 +106,7 @@ def gather_imad(c: dict) -> int:
 
 def table_imad(c: dict) -> int:
     p = (c["table_add"] * PRODUCTS["add"]
-         + (c["table_madd"] + c["table_ecsm_madd"]) * PRODUCTS["madd"]
+         + c["table_madd"] * PRODUCTS["madd_acc"] + c["table_ecsm_madd"] * PRODUCTS["madd"]
          + c["table_dbl"] * PRODUCTS["dbl"] + c["table_norm"] * PRODUCTS["norm"]
          + c["table_norm_chain"] * PRODUCTS["norm_chain"]
          + c["table_affine"] * PRODUCTS["affine"])

@@ -520,58 +520,58 @@ __device__ __forceinline__ void lp_normalize(const uint4* src, int E, uint4* pre
     lp_normalize_back(src, E, pref, lane, acc, ones, store, shared);
 }
 
-// Normalises the E entries of a chain P_e = P_{e-1} + Q_e (lane-planar
-// Jacobian in src) whose step ratios r_e = Z_e / Z_{e-1} were stored as
-// entry e of rat (jac_madd_ratio), so that Z_e = r_0 r_1 ... r_e and zlast =
-// Z_{E-1}: one warp-wide inversion of zlast, then going backwards Z_e^-1 is
-// in hand and Z_{e-1}^-1 = Z_e^-1 r_e, 4M + 1S per entry in all, and only
-// X, Y and r are read back.  Each lane's ok says whether its ratios are all
-// defined; if any lane's are not, the whole warp normalises the general way
-// (Montgomery's trick over the stored Z's, overwriting rat).  ones: every
-// ratio of this lane is 1 (so every Z is 1).  All 32 lanes call with the
-// same E.
+// Normalises the E entries of a chain kept as (X, Y, ZZ, ZZZ)
+// (jacz_madd_ratio): entry e holds X and Y in quads 0-3 of its 6-quad
+// lane-planar slot in src and its ZZZ factor rr3_e in quads 4-5, and its ZZ
+// factor rr2_e is entry e of rat, so ZZ_e = rr2_0 ... rr2_e (likewise ZZZ);
+// zz, zzz are those of the last entry.  One inversion of zz zzz gives both
+// ZZ^-1 and ZZZ^-1 of the last entry; going backwards each step multiplies
+// them by the entry's factors: 4M per entry in all.  ones: every factor of
+// this lane is 1.  With `shared` all threads of the block must call.
 template <class Store>
-__device__ __forceinline__ void lp_normalize_ratio(const uint4* src, int E, uint4* rat, unsigned lane,
-                                                   const fe& zlast, bool ones, bool ok, Store store,
-                                                   bool shared) {
+__device__ __forceinline__ void lp_normalize_zz(const uint4* src, int E, const uint4* rat, unsigned lane,
+                                                const fe& zz, const fe& zzz, bool ones, Store store,
+                                                bool shared) {
     if (E <= 0) return;
-    if (!group_all(ok, shared)) {
-        lp_normalize(src, E, rat, lane, store, shared);
-        return;
-    }
     if (group_all(ones, shared)) {
         for (int e = 0; e < E; e++) {
-            jac Pe;
-            lp_load_jac(Pe, src, e, lane);
+            const uint4* b = src + (size_t)e * 6 * 32 + lane;
             aff out;
-            fe_canon(out.x, Pe.X);
-            fe_canon(out.y, Pe.Y);
+            fe_from_quads(out.x, b[0], b[32]);
+            fe_from_quads(out.y, b[64], b[96]);
+            fe_canon(out.x, out.x);
+            fe_canon(out.y, out.y);
             store(e, out);
         }
         return;
     }
     fe inv;
-    group_inverse(inv, zlast, shared);
+    group_inverse(inv, fmul(zz, zzz), shared);
+    fe zzinv = fmul(inv, zzz);
+    fe zzzinv = fmul(inv, zz);
     for (int e = E - 1; e >= 0; e--) {
         if (e >= 2) {
-            // lanes 0-15: the X and Y lines of entry e - 2; 16-23: its ratio.
-            const char* line = lane < 16u ? (const char*)(src + (size_t)(e - 2) * 192) + lane * 128u
-                                          : (lane < 24u ? (const char*)(rat + (size_t)(e - 2) * 64) +
-                                                              (lane - 16u) * 128u
-                                                        : nullptr);
-            if (line) asm volatile("prefetch.global.L2 [%0];" ::"l"(line));
+            // lanes 0-23: the 24 lines of slot e - 2; 24-31: its ZZ factor.
+            const char* line = lane < 24u ? (const char*)(src + (size_t)(e - 2) * 192) + lane * 128u
+                                          : (const char*)(rat + (size_t)(e - 2) * 64) + (lane - 24u) * 128u;
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(line));
         }
         const uint4* b = src + (size_t)e * 6 * 32 + lane;
-        jac Pe;
-        fe_from_quads(Pe.X, b[0], b[32]);
-        fe_from_quads(Pe.Y, b[64], b[96]);
+        fe X, Y;
+        fe_from_quads(X, b[0], b[32]);
+        fe_from_quads(Y, b[64], b[96]);
         aff out;
-        jac_to_aff_with_zinv(out, Pe, inv);
+        out.x = fmul(X, zzinv);
+        out.y = fmul(Y, zzzinv);
+        fe_canon(out.x, out.x);
+        fe_canon(out.y, out.y);
         store(e, out);
         if (e > 0) {
-            fe r;
-            lp_load_fe(r, rat, e, lane);
-            inv = fmul(inv, r);
+            fe r2, r3;
+            lp_load_fe(r2, rat, e, lane);
+            fe_from_quads(r3, b[128], b[160]);
+            zzinv = fmul(zzinv, r2);
+            zzzinv = fmul(zzzinv, r3);
         }
     }
 }
@@ -656,30 +656,52 @@ __device__ __forceinline__ void table_item(const TableArgs& a, const PlanPtrs& P
         else lp_normalize(src, lens[1], pref, lane, store_l2, a.bshare);
         // Level 1: the multiples of the column's sorted distinct values,
         // with the forward pass of their normalisation.
-        // The step ratios of the chain go to pref, for the normalisation.
-        jac acc;
+        // The chain runs in (X, Y, ZZ, ZZZ) coordinates; each entry keeps X,
+        // Y and the factors its ZZ and ZZZ were multiplied by, for the
+        // normalisation.  A chain that meets infinity (an input at infinity)
+        // is recomputed in Jacobian coordinates and normalised the general way.
+        const uint16_t* ptr1 = col_level_ptr(P, col, 1);
+        jacz acc;
         bool cones = true, cok = true;
         {
-            const uint16_t* ptr = col_level_ptr(P, col, 1);
             aff D;
-            jac_set_inf(acc);
+            jacz_set_inf(acc);
             for (int e = 0; e < lens[0]; e++) {
-                lp_load_aff(D, l2aff, ptr[e], lane);
-                fe r;
-                jac_madd_ratio(acc, D, r, cok, e == 0);
-                lp_store_jac(coltab, e, lane, acc);
-                cones &= fe_is_one(r);
-                lp_store_fe(pref, e, lane, r);
+                lp_load_aff(D, l2aff, ptr1[e], lane);
+                fe r2, r3;
+                jacz_madd_ratio(acc, D, r2, r3, cok, e == 0);
+                uint4* b = coltab + (size_t)e * 6 * 32 + lane;
+                b[0] = fe_lo(acc.X);
+                b[32] = fe_hi(acc.X);
+                b[64] = fe_lo(acc.Y);
+                b[96] = fe_hi(acc.Y);
+                b[128] = fe_lo(r3);
+                b[160] = fe_hi(r3);
+                lp_store_fe(pref, e, lane, r2);
+                cones &= fe_is_one(r2) && fe_is_one(r3);
             }
         }
-        if (a.k == 1) {
-            // The column table is the strip table (E = lens[0] entries).
-            lp_normalize_ratio(coltab, E, pref, lane, acc.Z, cones, cok, store_table, a.bshare);
-            return;
+        const bool chain_ok = group_all(cok, a.bshare);
+        if (!chain_ok) {
+            jac accj;
+            aff D;
+            jac_set_inf(accj);
+            for (int e = 0; e < lens[0]; e++) {
+                lp_load_aff(D, l2aff, ptr1[e], lane);
+                jac_madd(accj, D);
+                lp_store_jac(coltab, e, lane, accj);
+            }
         }
         uint4* ca = colaff + (size_t)t * a.n1max * 128;
-        lp_normalize_ratio(coltab, lens[0], pref, lane, acc.Z, cones, cok,
-                           [&](int e, const aff& q) { lp_store_aff(ca, e, lane, q); }, a.bshare);
+        auto store_col = [&](int e, const aff& q) { lp_store_aff(ca, e, lane, q); };
+        if (a.k == 1) {
+            // The column table is the strip table (E = lens[0] entries).
+            if (chain_ok) lp_normalize_zz(coltab, E, pref, lane, acc.ZZ, acc.ZZZ, cones, store_table, a.bshare);
+            else lp_normalize(coltab, E, pref, lane, store_table, a.bshare);
+            return;
+        }
+        if (chain_ok) lp_normalize_zz(coltab, lens[0], pref, lane, acc.ZZ, acc.ZZZ, cones, store_col, a.bshare);
+        else lp_normalize(coltab, lens[0], pref, lane, store_col, a.bshare);
     }
     if (bad) {
         if (lane == 0) atomicOr(P.status, DEV_ERR_PLAN);

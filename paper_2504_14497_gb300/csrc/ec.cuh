@@ -127,57 +127,6 @@ __device__ __forceinline__ void jac_madd(jac& P, const aff& Q) {
     P.X = x3;
 }
 
-// jac_madd for a chain of additions (P_e = P_{e-1} + Q_e) that is later
-// normalised by walking the inverse of Z backwards: also returns r with
-// Z3 = r Z1 (H for an addition, 2 Y1 for a doubling, 1 when Q is infinity;
-// for the first step, from infinity, Z3 = 1 and r = 1).  ok is cleared when
-// no such r exists (P at infinity after the first step, or a result at
-// infinity); the caller then normalises the chain the general way.
-__device__ __forceinline__ void jac_madd_ratio(jac& P, const aff& Q, fe& r, bool& ok, bool first) {
-    fe_one(r);
-    if (aff_is_inf(Q)) {
-        if (jac_is_inf(P)) ok = false;
-        return;
-    }
-    if (jac_is_inf(P)) {
-        P.X = Q.x;
-        P.Y = Q.y;
-        fe_one(P.Z);
-        if (!first) ok = false;
-        return;
-    }
-    fe t1, t2, t3, t4, x3;
-    t1 = fsqr(P.Z);                  // Z1^2
-    t2 = fmul(t1, P.Z);              // Z1^3
-    t1 = fmul(t1, Q.x);              // U2
-    t2 = fmul(t2, Q.y);              // S2
-    fe_sub(t1, t1, P.X);             // H
-    fe_sub(t2, t2, P.Y);             // R
-    if (fe_is_zero(t1)) {
-        if (fe_is_zero(t2)) {        // same point: Z3 = 2 Y1 Z1
-            fe_add(r, P.Y, P.Y);
-            jac_dbl(P);
-            if (fe_is_zero(r) || jac_is_inf(P)) ok = false;
-        } else {                     // opposite points
-            jac_set_inf(P);
-            ok = false;
-        }
-        return;
-    }
-    r = t1;
-    P.Z = fmul(P.Z, t1);             // Z3 = Z1 H
-    t4 = fsqr(t1);                   // H^2
-    t3 = fmul(t4, t1);               // H^3
-    t4 = fmul(t4, P.X);              // X1 H^2
-    fe_add(t1, t4, t4);              // 2 X1 H^2
-    x3 = fsqr(t2);                   // R^2
-    fe_sub(x3, x3, t1);
-    fe_sub(x3, x3, t3);              // X3 = R^2 - 2 X1 H^2 - H^3
-    fe_sub(t4, t4, x3);              // X1 H^2 - X3
-    P.Y = fmulsub(t4, t2, t3, P.Y);  // Y3 = R (X1 H^2 - X3) - Y1 H^3
-    P.X = x3;
-}
-
 // Accumulator of a long run of mixed additions in which Z is never needed
 // itself: (X, Y, ZZ, ZZZ) with ZZ = Z^2 and ZZZ = Z^3 of some Jacobian Z
 // (infinity: ZZ = ZZZ = 0).  A mixed addition then updates ZZ and ZZZ with
@@ -242,6 +191,92 @@ __device__ __forceinline__ void jacz_madd(jacz& P, const aff& Q) {
     t3 = fmul(t4, t1);               // H^3
     P.ZZ = fmul(P.ZZ, t4);           // ZZ3 = ZZ1 H^2
     P.ZZZ = fmul(P.ZZZ, t3);         // ZZZ3 = ZZZ1 H^3
+    t4 = fmul(t4, P.X);              // X1 H^2
+    fe_add(t1, t4, t4);              // 2 X1 H^2
+    x3 = fsqr(t2);                   // R^2
+    fe_sub(x3, x3, t1);
+    fe_sub(x3, x3, t3);              // X3 = R^2 - 2 X1 H^2 - H^3
+    fe_sub(t4, t4, x3);              // X1 H^2 - X3
+    P.Y = fmulsub(t4, t2, t3, P.Y);  // Y3 = R (X1 H^2 - X3) - Y1 H^3
+    P.X = x3;
+}
+
+// Doubling in (X, Y, ZZ, ZZZ) coordinates (dbl-2001-b with delta = ZZ): Z
+// would become 2 Y Z, so ZZ is multiplied by rr2 = 4 Y^2 and ZZZ by
+// rr3 = 8 Y^3; both factors are returned.
+__device__ __forceinline__ void jacz_dbl_ratio(jacz& P, fe& rr2, fe& rr3) {
+    fe gamma, beta, alpha, t0, t1;
+    gamma = fsqr(P.Y);
+    beta = fmul(P.X, gamma);
+    fe_sub(t0, P.X, P.ZZ);
+    fe_add(t1, P.X, P.ZZ);
+    alpha = fmul(t0, t1);
+    fe_add(t0, alpha, alpha);
+    fe_add(alpha, t0, alpha);        // alpha = 3 (X - ZZ)(X + ZZ)
+    fe_add(beta, beta, beta);
+    fe_add(beta, beta, beta);        // 4 beta
+    fe_add(rr2, gamma, gamma);
+    fe_add(rr2, rr2, rr2);           // 4 Y^2
+    t1 = fmul(P.Y, gamma);           // Y^3
+    fe_add(rr3, t1, t1);
+    fe_add(rr3, rr3, rr3);
+    fe_add(rr3, rr3, rr3);           // 8 Y^3
+    t0 = fsqr(alpha);
+    fe_sub(t0, t0, beta);
+    fe_sub(P.X, t0, beta);           // X3 = alpha^2 - 8 beta
+    fe_sub(t0, beta, P.X);
+    t0 = fmul(alpha, t0);            // alpha (4 beta - X3)
+    gamma = fsqr(gamma);
+    fe_add(gamma, gamma, gamma);
+    fe_add(gamma, gamma, gamma);
+    fe_add(gamma, gamma, gamma);     // 8 Y^4
+    fe_sub(P.Y, t0, gamma);          // Y3
+    P.ZZ = fmul(P.ZZ, rr2);
+    P.ZZZ = fmul(P.ZZZ, rr3);
+}
+
+// jacz_madd for a chain normalised by walking ZZ^-1 and ZZZ^-1 backwards:
+// also returns the factors rr2, rr3 that ZZ and ZZZ were multiplied by (H^2
+// and H^3 for an addition; for a doubling those of jacz_dbl_ratio; 1 when
+// Q is infinity; for the first step, from infinity, ZZ = ZZZ = 1 and the
+// factors are 1).  ok is cleared when no such factors exist (infinity
+// after the first step, or a result at infinity).
+__device__ __forceinline__ void jacz_madd_ratio(jacz& P, const aff& Q, fe& rr2, fe& rr3, bool& ok, bool first) {
+    fe_one(rr2);
+    fe_one(rr3);
+    if (aff_is_inf(Q)) {
+        if (fe_is_zero(P.ZZ)) ok = false;
+        return;
+    }
+    if (fe_is_zero(P.ZZ)) {
+        P.X = Q.x;
+        P.Y = Q.y;
+        fe_one(P.ZZ);
+        fe_one(P.ZZZ);
+        if (!first) ok = false;
+        return;
+    }
+    fe t1, t2, t3, t4, x3;
+    t1 = fmul(P.ZZ, Q.x);            // U2
+    t2 = fmul(P.ZZZ, Q.y);           // S2
+    fe_sub(t1, t1, P.X);             // H
+    fe_sub(t2, t2, P.Y);             // R
+    if (fe_is_zero(t1)) {
+        if (fe_is_zero(t2)) {        // same point
+            jacz_dbl_ratio(P, rr2, rr3);
+            if (fe_is_zero(rr2) || fe_is_zero(P.ZZ)) ok = false;
+        } else {                     // opposite points
+            jacz_set_inf(P);
+            ok = false;
+        }
+        return;
+    }
+    t4 = fsqr(t1);                   // H^2
+    t3 = fmul(t4, t1);               // H^3
+    rr2 = t4;
+    rr3 = t3;
+    P.ZZ = fmul(P.ZZ, t4);
+    P.ZZZ = fmul(P.ZZZ, t3);
     t4 = fmul(t4, P.X);              // X1 H^2
     fe_add(t1, t4, t4);              // 2 X1 H^2
     x3 = fsqr(t2);                   // R^2
