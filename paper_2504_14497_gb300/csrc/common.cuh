@@ -1,6 +1,8 @@
-// Helpers shared by the PC-MM kernels: status codes, warp-level batched
-// affine normalisation (Montgomery's simultaneous-inversion trick with
-// warp-shuffle prefix products), and the lane-planar scratch layout.
+// Helpers shared by the PC-MM kernels: status codes, the bounded device
+// wait, batched inversion (Montgomery's simultaneous-inversion trick with
+// warp-shuffle prefix products, optionally shared by the four warps of a
+// block), warp-level affine normalisation, and the lane-planar scratch
+// layout.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>

@@ -114,10 +114,11 @@ __global__ void __launch_bounds__(128) base_mul_kernel(const uint4* __restrict__
 
 // Jacobian ciphertexts -> canonical affine.  Thread t takes the G
 // ciphertexts i = g T + t (T threads in the grid, g < G; each g is a
-// coalesced sweep), that is 2G points, and the warp shares one field
-// inversion among its 64 G points, and the four warps of the block share
-// one (Montgomery's simultaneous inversion: prefix products across each
-// lane's points, across the warp by shuffles, across the block's warps).  The prefix products wait in the output's x words, which the
+// coalesced sweep), that is 2G points, and the block's 128 threads share
+// one field inversion among their 256 G points (Montgomery's simultaneous
+// inversion: prefix products across each lane's points, across the warp by
+// shuffles, across the block's four warps).
+// The prefix products wait in the output's x words, which the
 // backward pass overwrites point by point after reading them.
 __global__ void __launch_bounds__(128) normalize_kernel(const uint4* __restrict__ in, size_t count,
                                                         uint4* __restrict__ out, int G) {

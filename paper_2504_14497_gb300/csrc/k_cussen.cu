@@ -18,17 +18,23 @@
 //         names, and a running prefix sum of points turns the multiples of
 //         differences into the multiples of the level's sorted values.
 //         Level 1 is the per-column table v B_c^(kj) over the distinct values
-//         v of the column.  For strips of k > 1 columns, each distinct k-tuple
-//         adds its columns' entries.  The table is then normalised to affine
-//         coordinates in the same kernel (Montgomery's simultaneous inversion:
-//         per-lane prefix products, then warp-shuffle prefix products and one
-//         inversion per warp).
+//         v of the column, a chain of mixed additions in (X, Y, Z^2, Z^3).
+//         For strips of k > 1 columns, each distinct k-tuple adds its
+//         columns' entries (affine additions, one shared inversion per
+//         round).  The tables are normalised to affine coordinates in the
+//         same kernel: level 2 by Montgomery's simultaneous inversion, the
+//         level-1 chains by walking Z^-2 and Z^-3 back along the factors the
+//         chain multiplied them by; the inversion is shared by the lanes of
+//         a warp and, when the block's four warps follow one strip's plan,
+//         by the whole block.
 //  gather (one warp per output row i, component c and 32 output columns)
 //         C_ij += T_s[rank_s(i)] for every strip s: the "un-sort and re-insert
 //         duplicates" step of Algorithm 2 fused with the accumulation of
-//         Algorithm 3, one mixed addition per strip.  The rank is the same for
-//         the whole warp (one broadcast load); the 32 lanes' table entries are
-//         adjacent, so the four 16-byte loads per point are coalesced.
+//         Algorithm 3, one mixed addition per strip into an accumulator in
+//         (X, Y, Z^2, Z^3).  The rank is the same for the whole warp (one
+//         broadcast load); the 32 lanes' table entries are adjacent, so the
+//         four 16-byte loads per point are coalesced.  Small outputs split
+//         their strips over several warps (combine_kernel adds the parts).
 #include <cuda_runtime.h>
 
 #include "cussen_core.cuh"
