@@ -151,8 +151,15 @@ __device__ __forceinline__ void jacz_from_jac(jacz& R, const jac& P) {
 
 // Jacobian representative without an inversion: with Z' = ZZ ZZZ = Z^5,
 // X' = x Z'^2 = X ZZ^4 and Y' = y Z'^3 = Y ZZZ^4 (4S + 3M).  Infinity maps
-// to Z' = 0.
+// to Z' = 0.  An accumulator that only ever copied one affine point (ZZ and
+// ZZZ both exactly 1) is returned as it is.
 __device__ __forceinline__ void jac_from_jacz(jac& R, const jacz& P) {
+    if (fe_is_one(P.ZZ) && fe_is_one(P.ZZZ)) {
+        R.X = P.X;
+        R.Y = P.Y;
+        R.Z = P.ZZ;
+        return;
+    }
     fe t = fsqr(P.ZZ);
     t = fsqr(t);
     R.X = fmul(P.X, t);
