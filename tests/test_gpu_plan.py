@@ -10,42 +10,15 @@ import pytest
 
 from paper_2504_14497_gb300 import inputs, pcmm
 from tests.gpu_common import device, encrypt_gpu
+from tests.layout_mirror import NLEV, layout as _layout
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
-
-NLEV = 4
 
 
 @pytest.fixture(scope="module")
 def dev():
     return device()
-
-
-def _a256(x):
-    return (x + 255) & ~255
-
-
-def _level2_bound(w):
-    lim, d = (1 << w) - 1, 0
-    while (d + 1) * (d + 2) // 2 <= lim:
-        d += 1
-    return max(d, 1)
-
-
-def _layout(m, n, w, k):
-    L = dict(nstrips=(n + k - 1) // k, n1max=min((1 << w) - 1, m))
-    L["l2max"] = min(_level2_bound(w), L["n1max"])
-    L["emax"] = min((1 << (w * k)) - 1, m)
-    L["ptr_stride"] = L["n1max"] + (NLEV - 2) * L["l2max"]
-    off = 256
-    L["rank"] = off; off = _a256(off + L["nstrips"] * m * 2)
-    L["nent"] = off; off = _a256(off + L["nstrips"] * 4)
-    L["codes"] = off; off = _a256(off + L["nstrips"] * L["emax"] * 2)
-    L["len"] = off; off = _a256(off + n * NLEV * 2)
-    L["vN"] = off; off = _a256(off + n * L["l2max"] * 2)
-    L["ptr"] = off
-    return L
 
 
 def _u16(buf, off, count):
