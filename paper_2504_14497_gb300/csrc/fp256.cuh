@@ -524,34 +524,112 @@ static __device__ __noinline__ fe fsqr(fe a) {
     return r;
 }
 
-__device__ __forceinline__ void fe_sqr_n(fe& r, const fe& a, int n) {
-    r = fsqr(a);
-    for (int i = 1; i < n; i++) r = fsqr(r);
+// x <- x 2^-k mod p for canonical x and 1 <= k <= 31.  Since p = -1 mod
+// 2^32, x + (x mod 2^k) p is a multiple of 2^k, below 2^k p, so the shifted
+// sum is canonical again.
+__device__ __forceinline__ void fe_div_pow2(fe& x, unsigned k) {
+    const uint32_t q = x.v[0] & ((1u << k) - 1u);
+    // t = x + q p with p = 2^256 - 2^224 + 2^192 + 2^96 - 1 (words 0..7:
+    // ffffffff x3, 0 x2, 1, ffffffff; the 2^256 term lands in word 8).
+    uint32_t t[9];
+    uint64_t c = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        const uint64_t pj = (j < 3 || j == 7) ? 0xffffffffull : (j == 6 ? 1ull : 0ull);
+        c += (uint64_t)x.v[j] + (uint64_t)q * pj;
+        t[j] = (uint32_t)c;
+        c >>= 32;
+    }
+    t[8] = (uint32_t)c;
+#pragma unroll
+    for (int j = 0; j < 8; j++) x.v[j] = __funnelshift_r(t[j], t[j + 1], k);
 }
 
-// r = a^(p-2) = a^-1 for a != 0 (Fermat).  Addition chain over the runs of
-// ones in p - 2 = ffffffff 00000001 00000000^3 ffffffff ffffffff fffffffd
-// (hex, high to low): with x_k = a^(2^k - 1), build x2, x3, x6, x12, x15,
-// x30, x32, then 255 squarings and 12 multiplications in total.
+// r = a^-1 mod p for a != 0 mod p (0 gives 0), a weakly reduced; r is
+// canonical.  Binary extended Euclid: with u = a, v = p, x1 = 1, x2 = 0 the
+// invariants x1 a = u and x2 a = v (mod p) hold throughout; factors of two
+// leave u (or v) together with the same power of two from x1 (or x2), and
+// the smaller of two odd u, v is subtracted from the larger (their
+// difference is even), until one of them is 1.  About 2 log2 p steps of a
+// few 256-bit additions each, against the 267 dependent multiplications of
+// a Fermat power.
 static __device__ __noinline__ void fe_inv(fe& r, const fe& a) {
-    fe x2, x3, x6, x12, x15, x30, x32, t;
-    x2 = fmul(fsqr(a), a);                       // 2^2 - 1
-    x3 = fmul(fsqr(x2), a);                      // 2^3 - 1
-    fe_sqr_n(t, x3, 3);  x6 = fmul(t, x3);       // 2^6 - 1
-    fe_sqr_n(t, x6, 6);  x12 = fmul(t, x6);      // 2^12 - 1
-    fe_sqr_n(t, x12, 3); x15 = fmul(t, x3);      // 2^15 - 1
-    fe_sqr_n(t, x15, 15); x30 = fmul(t, x15);    // 2^30 - 1
-    fe_sqr_n(t, x30, 2); x32 = fmul(t, x2);      // 2^32 - 1
-    // bits 255..224: 32 ones; bits 223..192: 0...01
-    fe_sqr_n(t, x32, 32); t = fmul(t, a);
-    // bits 191..96: zeros
-    fe_sqr_n(t, t, 96);
-    // bits 95..32: 64 ones
-    fe_sqr_n(t, t, 32); t = fmul(t, x32);
-    fe_sqr_n(t, t, 32); t = fmul(t, x32);
-    // bits 31..0: 30 ones, then 0, 1
-    fe_sqr_n(t, t, 30); t = fmul(t, x30);
-    fe_sqr_n(t, t, 2);  r = fmul(t, a);
+    fe u, v, x1, x2;
+    fe_canon(u, a);
+    if ((u.v[0] | u.v[1] | u.v[2] | u.v[3] | u.v[4] | u.v[5] | u.v[6] | u.v[7]) == 0u) {
+        fe_zero(r);
+        return;
+    }
+    v.v[0] = v.v[1] = v.v[2] = 0xffffffffu;
+    v.v[3] = v.v[4] = v.v[5] = 0u;
+    v.v[6] = 1u;
+    v.v[7] = 0xffffffffu;
+    fe_one(x1);
+    fe_zero(x2);
+    // Each step removes a factor of two or shrinks u + v: the bound is never
+    // reached for a != 0 mod p.
+    for (int it = 0; it < 4096; it++) {
+        const bool u1 = ((u.v[0] ^ 1u) | u.v[1] | u.v[2] | u.v[3] | u.v[4] | u.v[5] | u.v[6] | u.v[7]) == 0u;
+        if (u1) break;
+        const bool v1 = ((v.v[0] ^ 1u) | v.v[1] | v.v[2] | v.v[3] | v.v[4] | v.v[5] | v.v[6] | v.v[7]) == 0u;
+        if (v1) {
+            x1 = x2;
+            break;
+        }
+        if (!(u.v[0] & 1u)) {
+            const unsigned k = u.v[0] ? (unsigned)(__ffs(u.v[0]) - 1) : 31u;
+#pragma unroll
+            for (int j = 0; j < 7; j++) u.v[j] = __funnelshift_r(u.v[j], u.v[j + 1], k);
+            u.v[7] >>= k;
+            fe_div_pow2(x1, k);
+            continue;
+        }
+        if (!(v.v[0] & 1u)) {
+            const unsigned k = v.v[0] ? (unsigned)(__ffs(v.v[0]) - 1) : 31u;
+#pragma unroll
+            for (int j = 0; j < 7; j++) v.v[j] = __funnelshift_r(v.v[j], v.v[j + 1], k);
+            v.v[7] >>= k;
+            fe_div_pow2(x2, k);
+            continue;
+        }
+        // d = u - v; if no borrow u <- d, x1 <- x1 - x2, else v <- -d, x2 <- x2 - x1.
+        fe d;
+        uint32_t bw;
+        asm("sub.cc.u32  %0, %9, %17;\n\t"
+            "subc.cc.u32 %1, %10, %18;\n\t"
+            "subc.cc.u32 %2, %11, %19;\n\t"
+            "subc.cc.u32 %3, %12, %20;\n\t"
+            "subc.cc.u32 %4, %13, %21;\n\t"
+            "subc.cc.u32 %5, %14, %22;\n\t"
+            "subc.cc.u32 %6, %15, %23;\n\t"
+            "subc.cc.u32 %7, %16, %24;\n\t"
+            "subc.u32    %8, 0, 0;"
+            : "=r"(d.v[0]), "=r"(d.v[1]), "=r"(d.v[2]), "=r"(d.v[3]), "=r"(d.v[4]), "=r"(d.v[5]),
+              "=r"(d.v[6]), "=r"(d.v[7]), "=r"(bw)
+            : "r"(u.v[0]), "r"(u.v[1]), "r"(u.v[2]), "r"(u.v[3]), "r"(u.v[4]), "r"(u.v[5]), "r"(u.v[6]),
+              "r"(u.v[7]), "r"(v.v[0]), "r"(v.v[1]), "r"(v.v[2]), "r"(v.v[3]), "r"(v.v[4]), "r"(v.v[5]),
+              "r"(v.v[6]), "r"(v.v[7]));
+        if (!bw) {
+            u = d;
+            fe_sub(x1, x1, x2);
+            fe_canon(x1, x1);
+        } else {
+            asm("sub.cc.u32  %0, 0, %0;\n\t"
+                "subc.cc.u32 %1, 0, %1;\n\t"
+                "subc.cc.u32 %2, 0, %2;\n\t"
+                "subc.cc.u32 %3, 0, %3;\n\t"
+                "subc.cc.u32 %4, 0, %4;\n\t"
+                "subc.cc.u32 %5, 0, %5;\n\t"
+                "subc.cc.u32 %6, 0, %6;\n\t"
+                "subc.u32    %7, 0, %7;"
+                : "+r"(d.v[0]), "+r"(d.v[1]), "+r"(d.v[2]), "+r"(d.v[3]), "+r"(d.v[4]), "+r"(d.v[5]),
+                  "+r"(d.v[6]), "+r"(d.v[7]));
+            v = d;
+            fe_sub(x2, x2, x1);
+            fe_canon(x2, x2);
+        }
+    }
+    r = x1;
 }
 
 // r = a b - c d (mod p) with a single reduction: the two 512-bit products
