@@ -28,6 +28,7 @@ from __future__ import annotations
 import numpy as np
 
 N_ITER = 4
+L2_CHAIN_MIN = 32   # level-2 lengths from which the table kernel builds level 2 as a chain
 PRODUCTS = {"madd": 592, "madd_acc": 584, "add": 884, "dbl": 372, "norm": 420, "norm_chain": 256,
             "affine": 356}
 IMAD_PER_PRODUCT = 2
@@ -49,14 +50,17 @@ def cussen_counts(A: np.ndarray, w: int, k: int, l: int, N: int = N_ITER) -> dic
     ciphertext components), as the table and gather kernels perform them:
 
     * ``table_dbl``/``table_ecsm_madd``: double-and-add of the level-N values;
-    * ``table_add``: prefix sums of levels N-1..2 (Jacobian + Jacobian);
-    * ``table_madd``: level-1 prefix sums (Jacobian + affine);
+    * ``table_add``: prefix sums of levels N-1..2 (Jacobian + Jacobian;
+      N-1..3 when level 2 has at least L2_CHAIN_MIN entries);
+    * ``table_madd``: level-1 prefix sums (and those of a long level 2)
+      over affine addends;
     * ``table_affine``: k-tuple sums, affine additions sharing one inversion
       per round;
-    * ``table_norm``: level-2 entries normalised to affine (simultaneous
-      inversion);
-    * ``table_norm_chain``: level-1 entries (the column tables when k > 1,
-      the strip tables when k = 1) normalised along their chain's ratios;
+    * ``table_norm``: level-2 entries (level-3 entries when level 2 is
+      long) normalised to affine by simultaneous inversion;
+    * ``table_norm_chain``: chain entries (level 1: the column tables when
+      k > 1, the strip tables when k = 1; a long level 2) normalised along
+      their chain's ratios;
     * ``gather_madd``: accumulations of table entries into the outputs.
     Additions with an identity operand are copies and are not counted."""
     A = np.asarray(A).astype(np.int64) & ((1 << w) - 1)
@@ -75,9 +79,17 @@ def cussen_counts(A: np.ndarray, w: int, k: int, l: int, N: int = N_ITER) -> dic
                 v = int(v)
                 tdbl += chains * (v.bit_length() - 1)
                 tecsm += chains * (bin(v).count("1") - 1)
-            tadd += chains * sum(max(x - 1, 0) for x in lens[1:-1])
             tmadd += chains * max(lens[0] - 1, 0)
-            norm += chains * (lens[1] if N > 1 else 0)
+            if N > 2 and lens[1] >= L2_CHAIN_MIN:
+                # long level 2: a chain of mixed additions over level 3
+                # normalised to affine, itself normalised along its ratios
+                tadd += chains * sum(max(x - 1, 0) for x in lens[2:-1])
+                tmadd += chains * max(lens[1] - 1, 0)
+                norm += chains * lens[2]
+                nchain += chains * lens[1]
+            else:
+                tadd += chains * sum(max(x - 1, 0) for x in lens[1:-1])
+                norm += chains * (lens[1] if N > 1 else 0)
             if kw > 1:
                 nchain += chains * lens[0]
         distinct = np.unique(codes[codes != 0])

@@ -576,6 +576,33 @@ __device__ __forceinline__ void lp_normalize_zz(const uint4* src, int E, const u
     }
 }
 
+// The chain P_e = P_{e-1} + A[ptr[e]] (e < len, P_{-1} at infinity) over
+// affine addends A (lane-planar, 4 quads per entry), in (X, Y, ZZ, ZZZ):
+// entry e's X, Y and ZZZ factor go to slot e of `slots` (6 quads), its ZZ
+// factor to entry e of rat, as lp_normalize_zz reads them.  acc ends as the
+// last entry; ones and ok as for jacz_madd_ratio.
+static __device__ __noinline__ void lp_affine_chain(const uint4* A, const uint16_t* ptr, int len, uint4* slots,
+                                                    uint4* rat, unsigned lane, jacz& acc, bool& ones, bool& ok) {
+    aff D;
+    jacz_set_inf(acc);
+    ones = true;
+    ok = true;
+    for (int e = 0; e < len; e++) {
+        lp_load_aff(D, A, ptr[e], lane);
+        fe r2, r3;
+        jacz_madd_ratio(acc, D, r2, r3, ok, e == 0);
+        uint4* b = slots + (size_t)e * 6 * 32 + lane;
+        b[0] = fe_lo(acc.X);
+        b[32] = fe_hi(acc.X);
+        b[64] = fe_lo(acc.Y);
+        b[96] = fe_hi(acc.Y);
+        b[128] = fe_lo(r3);
+        b[160] = fe_hi(r3);
+        lp_store_fe(rat, e, lane, r2);
+        ones &= fe_is_one(r2) && fe_is_one(r3);
+    }
+}
+
 // One warp per (strip, component c, 32 output columns); all lanes follow the
 // same plan, so the control flow is warp-uniform.
 // Table of one warp item (strip, component, 32 output columns) of a chunk;
@@ -631,13 +658,17 @@ __device__ __forceinline__ void table_item(const TableArgs& a, const PlanPtrs& P
             lp_store_jac(src, e, lane, T);
         }
         uint4* alt = levB;
-        // Levels N-1..2: un-sort by the tracking pointers, then prefix sums.
-        // The last of them (level 2) also takes the forward pass of its
-        // normalisation.
+        // Levels N-1..2: un-sort by the tracking pointers, then prefix sums of
+        // Jacobian points; level 2 also takes the forward pass of its
+        // normalisation.  A long level 2 (wide values: hundreds of entries) is
+        // instead built like level 1, as a chain of mixed additions over its
+        // level 3 normalised to affine (plan data, so uniform over the strip).
+        const bool l2chain = NLEV > 2 && lens[1] >= 32;
+        auto store_l2 = [&](int e, const aff& q) { lp_store_aff(l2aff, e, lane, q); };
         fe pacc;
         bool pones = true;
         fe_one(pacc);
-        for (int lev = NLEV - 1; lev >= 2; lev--) {
+        auto jacobian_level = [&](int lev) {
             const uint16_t* ptr = col_level_ptr(P, col, lev);
             jac acc, D;
             jac_set_inf(acc);
@@ -647,13 +678,30 @@ __device__ __forceinline__ void table_item(const TableArgs& a, const PlanPtrs& P
                 lp_store_jac(alt, e, lane, acc);
                 if (lev == 2) lp_pref_step(pacc, pones, acc.Z, pref, e, lane);
             }
+        };
+        for (int lev = NLEV - 1; lev >= (l2chain ? 3 : 2); lev--) {
+            jacobian_level(lev);
             uint4* tmp = src; src = alt; alt = tmp;
         }
-        // Level 2 (multiples of the level-1 differences) to affine, so that
-        // the level-1 prefix sums are mixed additions.
-        auto store_l2 = [&](int e, const aff& q) { lp_store_aff(l2aff, e, lane, q); };
-        if (NLEV > 2) lp_normalize_back(src, lens[1], pref, lane, pacc, pones, store_l2, a.bshare);
-        else lp_normalize(src, lens[1], pref, lane, store_l2, a.bshare);
+        if (!l2chain) {
+            // Level 2 (multiples of the level-1 differences) to affine, so that
+            // the level-1 prefix sums are mixed additions.
+            if (NLEV > 2) lp_normalize_back(src, lens[1], pref, lane, pacc, pones, store_l2, a.bshare);
+            else lp_normalize(src, lens[1], pref, lane, store_l2, a.bshare);
+        } else {
+            // Level 3 (Jacobian, in src) to affine in l2aff, then level 2 as a
+            // chain over it into alt; l2aff then receives level 2.
+            lp_normalize(src, lens[2], pref, lane, store_l2, a.bshare);
+            jacz acc2;
+            bool ones2, ok2;
+            lp_affine_chain(l2aff, col_level_ptr(P, col, 2), lens[1], alt, pref, lane, acc2, ones2, ok2);
+            if (group_all(ok2, a.bshare)) {
+                lp_normalize_zz(alt, lens[1], pref, lane, acc2.ZZ, acc2.ZZZ, ones2, store_l2, a.bshare);
+            } else {
+                jacobian_level(2);
+                lp_normalize_back(alt, lens[1], pref, lane, pacc, pones, store_l2, a.bshare);
+            }
+        }
         // Level 1: the multiples of the column's sorted distinct values,
         // with the forward pass of their normalisation.
         // The chain runs in (X, Y, ZZ, ZZZ) coordinates; each entry keeps X,
@@ -662,25 +710,8 @@ __device__ __forceinline__ void table_item(const TableArgs& a, const PlanPtrs& P
         // is recomputed in Jacobian coordinates and normalised the general way.
         const uint16_t* ptr1 = col_level_ptr(P, col, 1);
         jacz acc;
-        bool cones = true, cok = true;
-        {
-            aff D;
-            jacz_set_inf(acc);
-            for (int e = 0; e < lens[0]; e++) {
-                lp_load_aff(D, l2aff, ptr1[e], lane);
-                fe r2, r3;
-                jacz_madd_ratio(acc, D, r2, r3, cok, e == 0);
-                uint4* b = coltab + (size_t)e * 6 * 32 + lane;
-                b[0] = fe_lo(acc.X);
-                b[32] = fe_hi(acc.X);
-                b[64] = fe_lo(acc.Y);
-                b[96] = fe_hi(acc.Y);
-                b[128] = fe_lo(r3);
-                b[160] = fe_hi(r3);
-                lp_store_fe(pref, e, lane, r2);
-                cones &= fe_is_one(r2) && fe_is_one(r3);
-            }
-        }
+        bool cones, cok;
+        lp_affine_chain(l2aff, ptr1, lens[0], coltab, pref, lane, acc, cones, cok);
         const bool chain_ok = group_all(cok, a.bshare);
         if (!chain_ok) {
             jac accj;

@@ -74,12 +74,15 @@ def test_wide_many_rows(dev):
     assert mismatches(got, want) == 0
 
 
-@pytest.mark.parametrize("mode", ["equal", "cancel", "infinity"])
-def test_wide_exceptional_additions(dev, mode):
+@pytest.mark.parametrize("mode,m,w", [("equal", 12, 12), ("cancel", 12, 12), ("infinity", 12, 12),
+                                      ("infinity", 80, 16), ("equal", 80, 16)])
+def test_wide_exceptional_additions(dev, mode, m, w):
     # Enc(B) replaced by points u G of chosen discrete logs so that equal
     # points, opposite points and infinity meet inside the table build and
-    # the gather; the expected product is (sum_k a_ik u_kj) G.
-    m, n, l, w = 12, 6, 3, 12
+    # the gather; the expected product is (sum_k a_ik u_kj) G.  With 80
+    # rows of 16-bit values level 2 is long enough to be built as a chain
+    # over an affine level 3, and infinity inputs send it down its fallback.
+    n, l = 6, 3
     rng = np.random.default_rng(1800)
     Ah = rng.integers(0, 1 << w, size=(m, n), dtype=np.uint16)
     Ah[:, 0] = np.arange(m, dtype=np.uint16) * 3        # an arithmetic column: equal differences
