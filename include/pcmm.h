@@ -277,7 +277,8 @@ pcmm_status pcmm_workspace_status(const void *ws, uint32_t *status_host, pcmm_st
 
 /* Normalises a Jacobian ciphertext array to canonical affine form
  * (Montgomery's simultaneous inversion: each thread takes up to 8
- * ciphertexts, one field inversion per warp, so per 64 to 512 points).
+ * ciphertexts, one field inversion per 128-thread block, so per 256 to
+ * 2048 points).
  * ct_jac: device, 48 * count words; ct_aff: device, 32 * count words
  * (may not overlap).  Errors: PCMM_EINVAL, PCMM_ECUDA. */
 pcmm_status pcmm_normalize(const uint32_t *ct_jac, size_t count, uint32_t *ct_aff,
