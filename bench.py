@@ -48,16 +48,21 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-schoolbook", action="store_true")
-    ap.add_argument("--workload", choices=["large", "serving", "batched", "sweep", "vector"], default="large",
+    ap.add_argument("--workload", choices=["large", "serving", "batched", "sweep", "vector", "decrypt", "sparse"],
+                    default="large",
                     help="large: the single large PC-MM (the headline line); serving: Poisson "
                          "request sweep of encrypted linear layers; batched: 64 uneven instances; "
                          "sweep: square PC-MM over n and w, Cussen beside schoolbook; vector: "
-                         "plaintext vector times ciphertext scalars")
+                         "plaintext vector times ciphertext scalars; decrypt: baby-step "
+                         "giant-step decryption of the large w = 8 product's output; sparse: the "
+                         "large product with mostly-zero A")
     ap.add_argument("--sweep-n", default="128,256,512,1024,2048")
     ap.add_argument("--sweep-widths", default="1,2,3,4,5,6,7,8,12,16")
     ap.add_argument("--vector-n", default="8,16,32,64,128,256,512")
     ap.add_argument("--vector-widths", default="4,8,12,16")
     ap.add_argument("--vector-scalars", type=int, default=65536)
+    ap.add_argument("--sparse-densities", default="1,0.5,0.2,0.1,0.05,0.02,0.01")
+    ap.add_argument("--sparse-widths", default="8,4")
     ap.add_argument("--rates", default="10,20,50,100,200,500,1000,2000")
     ap.add_argument("--seconds", type=float, default=2.0, help="arrival window per rate (serving)")
     return ap.parse_args()
@@ -638,6 +643,148 @@ def run_vector(args, dist):
             "rows": rows, "n_gpus": 1, "data": "synthetic (seeded)"}
 
 
+def run_sparse(args, dist):
+    """The large product 1024 x 1024 x 256 with a sparse A (entries non-zero
+    with probability rho, e.g. pruned weights): zero entries cost no point
+    addition in the gather (their rank is skipped) and no table entry, so
+    the time should follow the additions performed.  Per (w, rho): Cussen
+    time (cost-model k, best of two after a warm-up), point additions
+    performed and their rate, and the time relative to the dense matrix."""
+    import torch
+
+    from paper_2504_14497_gb300 import build, counts, inputs, pcmm
+
+    build.build()
+    torch.cuda.set_device(dist.local)
+    dev = torch.device("cuda", dist.local)
+    pcmm.init(dist.local)
+    m, n, l = 1024, 1024, 256
+    pr = inputs.pcmm_problem(SEED, 1, n, l, 1)
+    tab = pcmm.keytable(pcmm.public_key(pr["sk"], device=dev), device=dev)
+    ctB = pcmm.encrypt(tab, torch.from_numpy(pr["B"].reshape(-1)).to(dev),
+                       pcmm.to_device_words(pcmm.scalars_to_planar(pr["r"]), dev))
+    out = torch.empty(48 * m * l, dtype=torch.int32, device=dev)
+    cur = torch.cuda.current_stream()
+
+    def timed(fn, reps=2):
+        fn()
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(cur)
+            fn()
+            e1.record(cur)
+            e1.synchronize()
+            t = e0.elapsed_time(e1)
+            best = t if best is None else min(best, t)
+        return best
+
+    rows = []
+    for w in (int(x) for x in args.sparse_widths.split(",")):
+        k = pcmm.choose_k(m, n, l, w)
+        ws = pcmm.workspace(m, n, l, w, k, device=dev)
+        dense_ms = None
+        for rho in (float(x) for x in args.sparse_densities.split(",")):
+            A_h = inputs.sparse_plaintext(SEED + 11, m, n, w, rho)
+            A = torch.from_numpy(A_h).to(dev)
+            ms = timed(lambda: pcmm.cussen(A, ctB, l, w, k=k, ws=ws, out=out))
+            if pcmm.workspace_status(ws) != 0:
+                raise RuntimeError(f"device status at w={w} rho={rho}")
+            ops = counts.point_ops(counts.cussen_counts(A_h, w, k, l))
+            dense_ms = ms if dense_ms is None else dense_ms
+            rows.append({"w": w, "k": k, "density": rho, "nonzero_frac": float((A_h != 0).mean()),
+                         "cussen_ms": ms, "point_adds": ops, "point_adds_per_s": ops / (ms / 1e3),
+                         "time_vs_first": ms / dense_ms})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+        del ws
+        torch.cuda.empty_cache()
+    return {"workload": f"sparse: A {m}x{n} with entries non-zero with probability rho (uniform non-zero "
+                        f"w-bit values) x Enc(B) {n}x{l} (8-bit messages), cost-model k",
+            "metric": "Cussen PC-MM time per density", "unit": "ms", "rows": rows, "n_gpus": 1,
+            "data": "synthetic (seeded)"}
+
+
+def run_decrypt(args, dist):
+    """Decryption of a PC-MM result by its key owner (Section 2.4): the
+    1024 x 256 output of the large w = 8 product (262144 ciphertexts,
+    messages up to n 255 255), decrypted on the GPU by baby-step giant-step
+    with the default baby-step table (2^24 steps, four giant steps at most).
+    Times the table build once and the decryption of every output over
+    several steps (CUDA events), checks every message against the integer
+    product A B, and times the CPU oracle's decryption on a bounded sample
+    of the same ciphertexts."""
+    import torch
+
+    from paper_2504_14497_gb300 import build, counts, inputs, pcmm
+
+    build.build()
+    torch.cuda.set_device(dist.local)
+    dev = torch.device("cuda", dist.local)
+    pcmm.init(dist.local)
+    props = torch.cuda.get_device_properties(dev)
+    m, n, l, w = 1024, 1024, 256, 8
+    pr = inputs.pcmm_problem(SEED, m, n, l, w)
+    tab = pcmm.keytable(pcmm.public_key(pr["sk"], device=dev), device=dev)
+    ctB = pcmm.encrypt(tab, torch.from_numpy(pr["B"].reshape(-1)).to(dev),
+                       pcmm.to_device_words(pcmm.scalars_to_planar(pr["r"]), dev))
+    A = torch.from_numpy(pr["A"]).to(dev)
+    ct = pcmm.normalize(pcmm.cussen(A, ctB, l, w), m * l)
+    del ctB
+    torch.cuda.empty_cache()
+    count, mmax = m * l, n * (2**w - 1) * 255
+    cur = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(cur)
+    steps = pcmm.BabySteps.for_range(mmax, device=dev)
+    e1.record(cur)
+    e1.synchronize()
+    build_ms = e0.elapsed_time(e1)
+    out = torch.empty(count, dtype=torch.int64, device=dev)
+    for _ in range(max(args.warmup, 1)):
+        pcmm.decrypt(pr["sk"], ct, count, mmax, steps, out=out)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dist.local)
+    clocks.start()
+    e0.record(cur)
+    for _ in range(args.steps):
+        pcmm.decrypt(pr["sk"], ct, count, mmax, steps, out=out)
+    e1.record(cur)
+    e1.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    AB = pr["A"].astype(np.int64) @ pr["B"].astype(np.int64)
+    got = out.cpu().numpy().reshape(m, l)
+    if not (got == AB).all():
+        raise RuntimeError(f"decryption differs from A B at {int((got != AB).sum())} outputs")
+    from oracle import oracle
+    sk_int = oracle.words_to_int(pr["sk"])
+    prod = counts.decrypt_products(sk_int, AB, steps.baby)
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak = props.multi_processor_count * IMAD_PER_SM_PER_CLK * sm_max * 1e6
+    imad_rate = count * prod * counts.IMAD_PER_PRODUCT / (ms / 1e3)
+    cpu = None
+    if not args.no_cpu_baseline:
+        ns = 512
+        aos = pcmm.planar_to_ct(pcmm.to_host_words(ct), count)[:ns]
+        t0 = time.perf_counter()
+        dec = oracle.decrypt(pr["sk"], aos, mmax)
+        sec = time.perf_counter() - t0
+        if not (dec == AB.reshape(-1)[:ns]).all():
+            raise RuntimeError("oracle decryption differs from A B")
+        cpu = {"value": ns / sec, "unit": "decryptions/s", "cores": oracle.threads(), "kind": "oracle",
+               "sample": f"the first {ns} of the {count} output ciphertexts ({sec:.1f} s)"}
+    return {"workload": f"decrypt: the {m}x{l} output of the w = {w} PC-MM {m}x{n} x Enc({n}x{l}), "
+                        f"messages in [0, {mmax}], baby-step giant-step with {steps.baby} baby steps",
+            "metric": "decryptions per second", "unit": "decryptions/s", "value": count / (ms / 1e3),
+            "ms_per_step": ms, "steps": args.steps, "baby_table_build_ms": build_ms,
+            "baby_table_bytes": steps.table.numel(), "verified_against_AB": True,
+            "roofline": {"bound": "alu", "achieved": imad_rate / 1e12, "peak": peak / 1e12,
+                         "unit": "T IMAD/s", "frac": imad_rate / peak,
+                         "products_per_decryption": prod},
+            "clocks": clk, "cpu_baseline": cpu, "n_gpus": 1, "data": "synthetic (seeded)"}
+
+
 SERVING_MODELS = {"mlp_784": (256, 784), "mlp_256": (128, 256), "mlp_out": (10, 128)}
 
 
@@ -744,6 +891,10 @@ def main():
             out = run_sweep(args, dist)
         elif args.workload == "vector":
             out = run_vector(args, dist)
+        elif args.workload == "decrypt":
+            out = run_decrypt(args, dist)
+        elif args.workload == "sparse":
+            out = run_sparse(args, dist)
         else:
             out = run_ours(args, dist)
         if dist.rank == 0 and out is not None:

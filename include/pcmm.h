@@ -115,6 +115,43 @@ pcmm_status pcmm_base_mul(const uint32_t *scalars, size_t count, uint32_t *point
                           pcmm_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Decryption (Section 2.4): the key owner recovers m from (C1, C2) as the
+ * discrete logarithm of M = C2 - x C1 = m G, searched in [0, mmax] by
+ * baby-step giant-step.  A baby-step table holds j G for j in [1, baby)
+ * keyed on the affine x coordinate; it does not depend on the key, so one
+ * table serves every decryption with the same baby.  Each ciphertext then
+ * takes floor(mmax / baby) + 1 giant steps at most.
+ * ---------------------------------------------------------------------- */
+
+/* A baby-step count for messages in [0, mmax]: the smallest power of two
+ * >= mmax + 1, at least 32 and at most 2^24 (0 if mmax < 0). */
+uint32_t pcmm_bsgs_default_baby(int64_t mmax);
+
+/* Bytes of the baby-step table for 1 <= baby <= 2^24 (a hash table of 8-byte
+ * slots, at least 2 * baby of them; 0 for an invalid baby). */
+size_t pcmm_bsgs_bytes(uint32_t baby);
+
+/* Builds the baby-step table: j G for j in [1, baby).
+ * table: device, 16-byte aligned, at least pcmm_bsgs_bytes(baby) bytes;
+ * written (cleared first).  Requires pcmm_init on the current device.
+ * Errors: PCMM_EINVAL (baby outside [1, 2^24], null or misaligned table, no
+ * pcmm_init), PCMM_ENOMEM (table_bytes too small), PCMM_ECUDA. */
+pcmm_status pcmm_bsgs_build(uint32_t baby, void *table, size_t table_bytes, pcmm_stream_t stream);
+
+/* Decrypts count ciphertexts: out[i] = m in [0, mmax] with C2 - x C1 = m G,
+ * or -1 when no such m exists (the message is outside the range).
+ * sk_host: host, 8 words, the secret key x with 1 <= x < q.
+ * ct: device, affine ciphertext array of count elements (32 * count words).
+ * baby, table: a table built by pcmm_bsgs_build with the same baby (read
+ * only).  0 <= mmax <= 2^62.  out: device int64[count], written.
+ * Errors: PCMM_EINVAL (null or misaligned pointers, x = 0 or x >= q, mmax
+ * out of range, baby outside [1, 2^24], no pcmm_init), PCMM_ENOMEM
+ * (table_bytes too small), PCMM_ECUDA. */
+pcmm_status pcmm_decrypt(const uint32_t *sk_host, const uint32_t *ct, size_t count, int64_t mmax,
+                         uint32_t baby, const void *table, size_t table_bytes, int64_t *out,
+                         pcmm_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * PC-MM.  Inputs: A (device uint8 m x n, entries < 2^w), ctB (device affine
  * ciphertext matrix n x l).  Output: ctC (device Jacobian ciphertext matrix
  * m x l, 48 * m * l words), C_ij = sum_k a_ik (B1_kj, B2_kj).

@@ -136,3 +136,40 @@ def schoolbook_counts(A: np.ndarray, l: int) -> dict:
     rows_nnz = (A != 0).sum(axis=1)
     return {"dbl": chains * int(bl.sum()), "madd": chains * int((pc - 1).sum()),
             "add": chains * int(np.maximum(rows_nnz - 1, 0).sum())}
+
+
+def naf4(x: int) -> list:
+    """Width-4 non-adjacent form of x >= 0, least significant digit first
+    (digits in {0, +-1, +-3, +-5, +-7}): the recoding the decryption kernel's
+    scalar multiplication uses."""
+    d = []
+    while x > 0:
+        if x & 1:
+            r = x & 15
+            r = r - 16 if r >= 8 else r
+            x -= r
+        else:
+            r = 0
+        d.append(r)
+        x >>= 1
+    return d
+
+
+def decrypt_products(sk: int, msgs: np.ndarray, baby: int) -> float:
+    """Limb products per decryption, averaged over the messages (all in
+    range): the odd multiples of C1 (a doubling, three full additions, three
+    normalisations), x C1 (a doubling per NAF digit below the top, a mixed
+    addition per non-zero digit), M = C2 - x C1 (one mixed addition and a
+    normalisation), one giant step (mixed addition and normalisation) per
+    multiple of baby below m, and the check of the hit j G (one mixed
+    addition per non-zero byte of j; two multiplications and a squaring)."""
+    d = naf4(int(sk))
+    scalar = (len(d) - 1) * PRODUCTS["dbl"] + sum(1 for x in d if x) * PRODUCTS["madd"]
+    pre = PRODUCTS["dbl"] + 3 * PRODUCTS["add"] + 3 * PRODUCTS["norm"]
+    m = np.asarray(msgs, dtype=np.int64).reshape(-1)
+    steps = (m // baby).astype(np.float64)
+    j = m % baby
+    jbytes = sum(((j >> (8 * b)) & 255) != 0 for b in range(3)).astype(np.float64)
+    per = (pre + scalar + PRODUCTS["madd"] + PRODUCTS["norm"]
+           + steps * (PRODUCTS["madd"] + PRODUCTS["norm"]) + jbytes * PRODUCTS["madd"] + 2 * 64 + 36)
+    return float(per.mean())

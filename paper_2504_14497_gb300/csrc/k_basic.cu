@@ -2,16 +2,13 @@
 // for the device field and group arithmetic.
 #include <cuda_runtime.h>
 
+#include "comb.cuh"
 #include "common.cuh"
 #include "profiler.cuh"
 
 using namespace pcmm;
 
 namespace {
-
-constexpr int COMB_WINDOWS = 32;    // 8-bit windows of a 256-bit scalar
-constexpr int COMB_ENTRIES = 256;   // v = 0..255 per window (v = 0 unused)
-constexpr int COMB_POINTS = COMB_WINDOWS * COMB_ENTRIES;
 
 // Comb table of the generator, quad-planar with stride COMB_POINTS.
 __device__ uint4 g_comb_G[4 * COMB_POINTS];
@@ -263,6 +260,14 @@ inline unsigned grid_for(size_t count, unsigned block) { return (unsigned)((coun
 bool g_ready[64] = {false};
 
 }  // namespace
+
+const uint4* pcmm::comb_table_G() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || !g_ready[dev]) return nullptr;
+    uint4* tab = nullptr;
+    if (cudaGetSymbolAddress((void**)&tab, g_comb_G) != cudaSuccess) return nullptr;
+    return tab;
+}
 
 extern "C" int pcmm_version(void) { return 10000; }
 

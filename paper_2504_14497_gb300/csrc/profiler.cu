@@ -18,7 +18,8 @@ std::vector<Slot> g_slots;
 int g_used = 0;
 bool g_on = false;
 const char* const g_names[KID_COUNT] = {"plan", "table", "gather", "normalize",
-                                        "encrypt", "schoolbook", "comb", "batched", "combine"};
+                                        "encrypt", "schoolbook", "comb", "batched", "combine",
+                                        "bsgs", "decrypt"};
 }  // namespace
 
 ProfScope::ProfScope(int kernel_id, cudaStream_t s) : slot(-1), stream(s) {

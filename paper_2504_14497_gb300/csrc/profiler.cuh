@@ -15,7 +15,9 @@ enum KernelId {
     KID_COMB = 6,
     KID_BATCHED = 7,
     KID_COMBINE = 8,
-    KID_COUNT = 9
+    KID_BSGS = 9,
+    KID_DECRYPT = 10,
+    KID_COUNT = 11
 };
 
 // Records a start event on construction and a stop event on destruction

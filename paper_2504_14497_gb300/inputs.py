@@ -59,6 +59,19 @@ def _plaintext(gen, m: int, n: int, w: int) -> np.ndarray:
     return gen.integers(0, 1 << w, size=(m, n), dtype=adt) if m * n else np.zeros((m, n), adt)
 
 
+def sparse_plaintext(seed: int, m: int, n: int, w: int, density: float) -> np.ndarray:
+    """A w-bit plaintext matrix whose entries are non-zero with probability
+    `density` (each independently), the non-zero values uniform over
+    [1, 2^w) (for example pruned weights)."""
+    if not 1 <= w <= 16 or not 0.0 <= density <= 1.0:
+        raise ValueError("w must be in [1, 16] and density in [0, 1]")
+    gen = streams(seed)["A"]
+    adt = np.uint8 if w <= 8 else np.uint16
+    vals = gen.integers(1, 1 << w, size=(m, n), dtype=adt)
+    keep = gen.random(size=(m, n)) < density
+    return np.where(keep, vals, 0).astype(adt)
+
+
 def plaintext_matrix(seed: int, m: int, n: int, w: int) -> np.ndarray:
     """The A of pcmm_problem(seed, m, n, l, w, ...), drawn alone."""
     if not 1 <= w <= 16:

@@ -26,7 +26,8 @@ PCMM_MAX_WK = 16       # strip code width w * k, bits
 # Names of every exported entry point, in the order of include/pcmm.h.
 EXPORTS = (
     "pcmm_version", "pcmm_status_string", "pcmm_init", "pcmm_keytable_bytes", "pcmm_keytable",
-    "pcmm_encrypt", "pcmm_base_mul", "pcmm_schoolbook", "pcmm_schoolbook16", "pcmm_cussen_choose_k",
+    "pcmm_encrypt", "pcmm_base_mul", "pcmm_bsgs_default_baby", "pcmm_bsgs_bytes", "pcmm_bsgs_build",
+    "pcmm_decrypt", "pcmm_schoolbook", "pcmm_schoolbook16", "pcmm_cussen_choose_k",
     "pcmm_cussen_workspace_bytes", "pcmm_cussen", "pcmm_cussen16", "pcmm_cussen_plan_bytes", "pcmm_cussen_plan", "pcmm_cussen_exec_bytes",
     "pcmm_cussen_execute", "pcmm_cussen_static", "pcmm_batched_workspace_bytes", "pcmm_batched_prepare", "pcmm_batched_run",
     "pcmm_workspace_status", "pcmm_copy_columns", "pcmm_normalize", "pcmm_profile_enable",
@@ -62,6 +63,10 @@ def lib():
                 "pcmm_keytable": ([u32p, vp, vp], ci),
                 "pcmm_encrypt": ([vp, vp, vp, sz, vp, vp], ci),
                 "pcmm_base_mul": ([vp, sz, vp, vp], ci),
+                "pcmm_bsgs_default_baby": ([ctypes.c_int64], ctypes.c_uint32),
+                "pcmm_bsgs_bytes": ([ctypes.c_uint32], sz),
+                "pcmm_bsgs_build": ([ctypes.c_uint32, vp, sz, vp], ci),
+                "pcmm_decrypt": ([u32p, vp, sz, ctypes.c_int64, ctypes.c_uint32, vp, sz, vp, vp], ci),
                 "pcmm_schoolbook": ([vp, ci, ci, ci, vp, ci, vp, vp], ci),
                 "pcmm_schoolbook16": ([vp, ci, ci, ci, vp, ci, vp, vp], ci),
                 "pcmm_cussen_choose_k": ([ci, ci, ci, ci], ci),
@@ -221,6 +226,49 @@ def public_key(sk_words: np.ndarray, device="cuda") -> np.ndarray:
     pts = base_mul(s, 1)
     torch.cuda.synchronize()
     return planar_to_points(to_host_words(pts).reshape(4, 1, 4))[0]
+
+
+# -------------------------------------------------------------- decryption
+
+class BabySteps:
+    """Baby-step table j G, j in [1, baby), for decryption by baby-step
+    giant-step (independent of the key: one table serves every call with
+    messages in [0, mmax] for any mmax)."""
+
+    def __init__(self, baby: int, device="cuda", stream=None):
+        torch = _torch()
+        L = lib()
+        nbytes = int(L.pcmm_bsgs_bytes(int(baby)))
+        if nbytes == 0:
+            raise ValueError(f"baby = {baby} outside [1, 2^24]")
+        self.baby = int(baby)
+        self.table = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        _check(L.pcmm_bsgs_build(self.baby, _ptr(self.table), nbytes, _stream(stream)),
+               "pcmm_bsgs_build")
+
+    @classmethod
+    def for_range(cls, mmax: int, device="cuda", stream=None):
+        """A table sized by the library's default for messages in [0, mmax]."""
+        baby = int(lib().pcmm_bsgs_default_baby(int(mmax)))
+        if baby == 0:
+            raise ValueError("mmax must be >= 0")
+        return cls(baby, device, stream)
+
+
+def decrypt(sk_words, ct, count: int, mmax: int, steps: BabySteps, out=None, stream=None):
+    """Messages of count affine ciphertexts (cuda int32[32 * count]) under
+    the secret key sk (uint32[8]): cuda int64[count], -1 where the message is
+    outside [0, mmax]."""
+    torch = _torch()
+    sk = np.ascontiguousarray(np.asarray(sk_words, dtype=np.uint32).reshape(8))
+    if ct.numel() < PCMM_AFF_WORDS * count:
+        raise ValueError("ct holds fewer than count ciphertexts")
+    if out is None:
+        out = torch.empty(count, dtype=torch.int64, device=ct.device)
+    _check(lib().pcmm_decrypt(sk.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), _ptr(ct), int(count),
+                              int(mmax), steps.baby, _ptr(steps.table), steps.table.numel(), _ptr(out),
+                              _stream(stream)), "pcmm_decrypt")
+    return out
 
 
 # ------------------------------------------------------------------ PC-MM

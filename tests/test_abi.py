@@ -64,6 +64,46 @@ def test_host_validation_without_gpu(lib):
     assert lib.pcmm_normalize(None, 4, None, None) == 1
 
 
+def test_decrypt_host_validation_without_gpu(lib):
+    # Baby-step sizing, and arguments rejected before any CUDA call.
+    assert lib.pcmm_bsgs_default_baby(-1) == 0
+    assert lib.pcmm_bsgs_default_baby(0) == 32
+    assert lib.pcmm_bsgs_default_baby(31) == 32
+    assert lib.pcmm_bsgs_default_baby(32) == 64
+    assert lib.pcmm_bsgs_default_baby(3600) == 4096
+    assert lib.pcmm_bsgs_default_baby(1024 * 255 * 255) == 1 << 24
+    assert lib.pcmm_bsgs_default_baby(1 << 40) == 1 << 24
+    assert lib.pcmm_bsgs_bytes(0) == 0
+    assert lib.pcmm_bsgs_bytes((1 << 24) + 1) == 0
+    assert lib.pcmm_bsgs_bytes(1) == 16
+    assert lib.pcmm_bsgs_bytes(7) == 128
+    assert lib.pcmm_bsgs_bytes(32) == 512
+    assert lib.pcmm_bsgs_bytes(1 << 24) == 8 << 25
+    d = ctypes.c_void_p(256)
+    assert lib.pcmm_bsgs_build(0, d, 1 << 20, None) == 1
+    assert lib.pcmm_bsgs_build(32, None, 1 << 20, None) == 1
+    assert lib.pcmm_bsgs_build(32, ctypes.c_void_p(264), 1 << 20, None) == 1   # misaligned
+    assert lib.pcmm_bsgs_build(32, d, 511, None) == 2
+    q = 0xFFFFFFFF00000000FFFFFFFFFFFFFFFFBCE6FAADA7179E84F3B9CAC2FC632551
+
+    def key(x):
+        return (ctypes.c_uint32 * 8)(*[(x >> (32 * i)) & 0xFFFFFFFF for i in range(8)])
+
+    def dec(x, mmax=100, baby=32, nbytes=512):
+        return lib.pcmm_decrypt(key(x), d, 4, mmax, baby, d, nbytes, d, None)
+
+    assert dec(0) == 1
+    assert dec(q) == 1
+    assert dec(q + 5) == 1
+    assert dec(5, mmax=-1) == 1
+    assert dec(5, mmax=(1 << 62) + 1) == 1
+    assert dec(5, baby=0) == 1
+    assert dec(5, baby=(1 << 24) + 1) == 1
+    assert dec(5, nbytes=511) == 2
+    assert dec(q - 1, nbytes=511) == 2
+    assert lib.pcmm_decrypt(None, d, 4, 100, 32, d, 512, d, None) == 1
+
+
 def test_cost_model_choices(lib):
     # Wide values: one column per strip; narrow values: wider strips.
     assert pcmm.choose_k(1024, 1024, 256, 8) == 1

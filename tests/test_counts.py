@@ -29,3 +29,21 @@ def test_schoolbook_counts():
     c = counts.schoolbook_counts(A, 2)
     # 1: 0 dbl; 3: 1 dbl + 1 madd; 4: 2 dbl; adds: row 0 has 2 terms -> 1.
     assert c == {"dbl": 4 * 3, "madd": 4 * 1, "add": 4 * 1}
+
+
+def test_naf4_recoding():
+    # The width-4 NAF: digits odd in [-7, 7] or zero, at most one non-zero
+    # digit in any four consecutive ones, top digit non-zero, value exact.
+    rng = np.random.default_rng(3)
+    xs = [1, 2, 7, 8, 9, 15, 16, 17, 255, 2**255, 2**256 - 1]
+    xs += [int.from_bytes(rng.bytes(32), "little") for _ in range(50)]
+    for x in xs:
+        d = counts.naf4(x)
+        assert sum(v << i for i, v in enumerate(d)) == x
+        assert all(v == 0 or (v % 2 == 1 and -7 <= v <= 7) for v in d)
+        assert all(sum(1 for v in d[i:i + 4] if v) <= 1 for i in range(len(d)))
+        assert d[-1] != 0 and len(d) <= x.bit_length() + 1
+    assert counts.naf4(0) == []
+    # About one non-zero digit in five for random 256-bit scalars.
+    nz = np.mean([sum(1 for v in counts.naf4(x) if v) for x in xs[11:]])
+    assert 45 < nz < 58

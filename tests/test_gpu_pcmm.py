@@ -104,6 +104,24 @@ def test_zero_matrix_and_zero_rows(dev):
     assert not got.any()
 
 
+@pytest.mark.parametrize("density,w", [(0.02, 8), (0.2, 4), (0.005, 1)])
+def test_sparse_plaintext(dev, density, w):
+    # Pruned-weight style A: most entries zero, whole zero strips for k > 1
+    # and rows with no non-zero entry at all.  Every output against the
+    # closed form, for k = 1, the cost-model k and a wide strip.
+    m, n, l = 150, 301, 70
+    pr = inputs.pcmm_problem(820 + w, m, n, l, w)
+    pr["A"] = inputs.sparse_plaintext(820 + w, m, n, w, density)
+    pr["A"][3] = 0
+    ctB = encrypt_gpu(dev, pr)
+    A = torch.from_numpy(pr["A"]).to(dev)
+    want = _want(pr)
+    for k in sorted({1, pcmm.choose_k(m, n, l, w), 16 // w if w > 1 else 8}):
+        got = run_affine(lambda: pcmm.cussen(A, ctB, l, w, k=k), m * l)
+        assert mismatches(got, want) == 0, k
+    assert not got.reshape(m, l, 2, 16)[3].any()
+
+
 def _crafted(seed, m, n, l, w, mode):
     """Enc(B) replaced by points u G of chosen discrete logs; the expected
     product (sum_k a_ik u_kj) G is computed by the oracle from the scalars."""
