@@ -152,10 +152,9 @@ __device__ __forceinline__ bool group_all(bool x, bool shared) {
 
 // Normalise E Jacobian points held in each lane's registers to canonical
 // affine coordinates; infinity (Z = 0) becomes (0, 0).  One inversion per
-// warp for 32 * E points (all 32 lanes must call), or with `shared` one per
-// 128-thread block (all 128 threads must call).
+// warp for 32 * E points.  All 32 lanes must call.
 template <int E>
-__device__ __forceinline__ void warp_normalize_regs(aff out[E], const jac P[E], bool shared = false) {
+__device__ __forceinline__ void warp_normalize_regs(aff out[E], const jac P[E]) {
     fe pref[E];
     fe acc;
     fe_one(acc);
@@ -167,7 +166,7 @@ __device__ __forceinline__ void warp_normalize_regs(aff out[E], const jac P[E], 
         pref[e] = acc;
     }
     fe inv;
-    group_inverse(inv, acc, shared);
+    warp_inverse(inv, acc);
 #pragma unroll
     for (int e = E - 1; e >= 0; e--) {
         fe zinv;

@@ -46,6 +46,38 @@ __device__ __forceinline__ void fe_neg(fe& r, const fe& a) {
     r = t;
 }
 
+// Normalise E Jacobian points held in each thread's registers to canonical
+// affine coordinates with one field inversion per 128-thread block
+// (infinity becomes (0, 0)).  All 128 threads of the block must call.
+template <int E>
+__device__ __forceinline__ void block_normalize_regs(aff out[E], const jac P[E]) {
+    fe pref[E];
+    fe acc;
+    fe_one(acc);
+#pragma unroll
+    for (int e = 0; e < E; e++) {
+        fe z = P[e].Z;
+        if (fe_is_zero(z)) fe_one(z);
+        acc = fmul(acc, z);
+        pref[e] = acc;
+    }
+    fe inv = block4_inverse(acc);
+#pragma unroll
+    for (int e = E - 1; e >= 0; e--) {
+        const fe zinv = e > 0 ? fmul(inv, pref[e - 1]) : inv;
+        fe z = P[e].Z;
+        const bool is_inf = fe_is_zero(z);
+        if (is_inf) fe_one(z);
+        inv = fmul(inv, z);
+        if (is_inf) {
+            fe_zero(out[e].x);
+            fe_zero(out[e].y);
+        } else {
+            jac_to_aff_with_zinv(out[e], P[e], zinv);
+        }
+    }
+}
+
 // Whether the Jacobian J and the affine A (not infinity) are the same point.
 __device__ __forceinline__ bool jac_equals_aff(const jac& J, const aff& A) {
     if (jac_is_inf(J)) return false;
@@ -65,7 +97,7 @@ __global__ void __launch_bounds__(128) bsgs_build_kernel(const uint4* __restrict
     jac R[1];
     comb_mul_u64(R[0], gtab, valid ? j : 1u, 3);
     aff A[1];
-    warp_normalize_regs<1>(A, R, true);   // every thread of the block reaches this
+    block_normalize_regs<1>(A, R);   // every thread of the block reaches this
     if (!valid) return;
     const unsigned long long val = ((unsigned long long)A[0].x.v[1] << 32) | (unsigned long long)(j + 1);
     uint32_t h = A[0].x.v[0] & mask;
@@ -88,7 +120,7 @@ static __device__ __noinline__ void odd_multiples(aff odd[4], const aff& C1) {
     jac_add(P[1], D);
     P[2] = P[1];
     jac_add(P[2], D);
-    warp_normalize_regs<3>(odd + 1, P, true);
+    block_normalize_regs<3>(odd + 1, P);
 }
 
 // The affine M = C2 - R (R Jacobian) and the giant stride -s G.  All 128
@@ -101,7 +133,7 @@ static __device__ __noinline__ void start_point(aff& M, aff& negS, jac R, const 
     J[0] = R;
     comb_mul_u64(J[1], gtab, s, 4);     // s <= 2^24: four comb windows
     aff A[2];
-    warp_normalize_regs<2>(A, J, true);
+    block_normalize_regs<2>(A, J);
     M = A[0];
     negS = A[1];
     fe_neg(negS.y, negS.y);
@@ -137,7 +169,7 @@ static __device__ __noinline__ void giant_step(aff& M, const aff& Q) {
     jac_from_aff(J[0], M);
     jac_madd(J[0], Q);
     aff A[1];
-    warp_normalize_regs<1>(A, J, true);
+    block_normalize_regs<1>(A, J);
     M = A[0];
 }
 
