@@ -196,8 +196,11 @@ size_t pcmm_cussen_workspace_bytes(int m, int n, int l, int w, int k);
  * ws: device workspace, 256-byte aligned, of at least
  * pcmm_cussen_workspace_bytes(m, n, l, w, k) bytes; its first 4 bytes are a
  * status word that kernels OR error bits into (1: an entry of A >= 2^w,
- * such entries are masked to w bits).  The status word is cleared at the
- * start of every call; read it with pcmm_workspace_status.
+ * such entries are masked to w bits; 2: a plan size exceeded its bound;
+ * 8, only in a library built with -DPCMM_DEBUG_BOUNDS: a plan index (row
+ * rank, tracking pointer, tuple component) outside the table it selects
+ * from, the access skipped).  The status word is cleared at the start of
+ * every call; read it with pcmm_workspace_status.
  * Errors: PCMM_EINVAL, PCMM_ENOMEM (workspace too small), PCMM_ECUDA. */
 pcmm_status pcmm_cussen(const uint8_t *A, int m, int n, int w, const uint32_t *ctB, int l,
                         uint32_t *ctC, int k, void *ws, size_t ws_bytes, pcmm_stream_t stream);

@@ -46,8 +46,12 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
-    if not force and up_to_date():
+def build(force: bool = False, verbose: bool = False, extra_flags=None, lib_path: str = LIB) -> str:
+    """Compiles every translation unit and links lib_path (by default the
+    in-tree libpcmm.so).  extra_flags go to every nvcc call, e.g.
+    ["-DPCMM_DEBUG_BOUNDS"] for a library whose kernels check every plan
+    index before using it (a separate lib_path keeps the product library)."""
+    if not force and lib_path == LIB and up_to_date():
         return LIB
     os.makedirs(BUILD_DIR, exist_ok=True)
     cc = nvcc()
@@ -56,8 +60,9 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
         flags += ["-Xptxas", "-v"]
     procs = []
     objs = []
+    tag = "" if lib_path == LIB else "_" + os.path.basename(lib_path).split(".")[0]
     for src in sources():
-        obj = os.path.join(BUILD_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(BUILD_DIR, os.path.basename(src)[:-3] + tag + ".o")
         objs.append(obj)
         cmd = [cc] + flags + ["-c", src, "-o", obj]
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -72,10 +77,10 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     if failed:
         msg = "\n".join(f"--- {s}\n{t}" for s, t in failed)
         raise RuntimeError(f"nvcc failed:\n{msg}")
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     subprocess.run([cc] + ARCH + ["-shared", "-o", tmp] + objs, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -17,6 +17,7 @@ enum : uint32_t {
     DEV_ERR_A_RANGE = 1u << 0,  // an entry of A is >= 2^w
     DEV_ERR_PLAN = 1u << 1,     // a plan size exceeded its bound
     DEV_ERR_TIMEOUT = 1u << 2,  // a bounded device-side wait gave up
+    DEV_ERR_BOUNDS = 1u << 3,   // a plan index outside its table (PCMM_DEBUG_BOUNDS builds)
 };
 
 // Waits until *ctr >= target, polling with short sleeps, for at most about

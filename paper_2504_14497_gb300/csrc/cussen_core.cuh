@@ -637,7 +637,7 @@ __device__ __forceinline__ void table_item(const TableArgs& a, const PlanPtrs& P
     auto store_table = [&](int e, const aff& q) {
         store_aff(a.table, a.table_points, ((tbase + e) * 2 + c) * a.lp + j, q);
     };
-    bool bad = false;
+    bool bad = false, dbad = false;
 
     for (int t = 0; t < kw; t++) {
         const int col = c0 + t;
@@ -649,6 +649,17 @@ __device__ __forceinline__ void table_item(const TableArgs& a, const PlanPtrs& P
         bad |= lens[0] > a.n1max;
 #pragma unroll
         for (int q = 1; q < NLEV; q++) bad |= lens[q] > a.l2max;
+#ifdef PCMM_DEBUG_BOUNDS
+        // Each tracking pointer of level lev (lens[lev-1] of them) names an
+        // entry of level lev + 1 (lens[lev] entries); for k = 1 the strip
+        // table is the column's level 1.
+        for (int lev = 1; lev < NLEV && !bad; lev++) {
+            const uint16_t* pl = col_level_ptr(P, col, lev);
+            for (int e = 0; e < lens[lev - 1]; e++) dbad |= pl[e] >= lens[lev];
+        }
+        if (a.k == 1) dbad |= E != lens[0];
+        bad |= dbad;
+#endif
         if (bad) break;
         // Level N: multiples of the compressed values (double-and-add).
         uint4* src = levA;
@@ -735,9 +746,23 @@ __device__ __forceinline__ void table_item(const TableArgs& a, const PlanPtrs& P
         else lp_normalize(coltab, lens[0], pref, lane, store_col, a.bshare);
     }
     if (bad) {
-        if (lane == 0) atomicOr(P.status, DEV_ERR_PLAN);
+        if (lane == 0) atomicOr(P.status, dbad ? DEV_ERR_BOUNDS : DEV_ERR_PLAN);
         return;
     }
+#ifdef PCMM_DEBUG_BOUNDS
+    // Every component of every tuple names an entry of its column table.
+    for (int e = 0; e < E && !dbad; e++) {
+        const uint32_t code = P.codes[(size_t)s * a.emax + e];
+        for (int t = 0; t < kw; t++) {
+            const uint32_t x = (code >> (a.w * t)) & amask;
+            if (x) dbad |= P.col_rank1[(size_t)(c0 + t) * 256 + x] >= P.col_len[(size_t)(c0 + t) * NLEV];
+        }
+    }
+    if (E > a.emax || dbad) {
+        if (lane == 0) atomicOr(P.status, DEV_ERR_BOUNDS);
+        return;
+    }
+#endif
     // k > 1: one entry per distinct k-tuple, the sum of its columns' (affine)
     // entries, computed in affine coordinates one addition round at a time:
     // round r adds the (r+1)-th non-zero component of every tuple that has
@@ -905,6 +930,12 @@ __device__ __forceinline__ void gather_item(const GatherArgs& a, const PlanPtrs&
     for (int sl = s_lo; sl < s_hi; sl++) {
         const uint16_t code = rk[(size_t)sl * a.m];
         if (code == NO_RANK) continue;
+#ifdef PCMM_DEBUG_BOUNDS
+        if (code >= P.nent[a.s0 + sl]) {   // a rank past the strip's table
+            atomicOr(P.status, DEV_ERR_BOUNDS);
+            continue;
+        }
+#endif
         const size_t ti = (((size_t)sl * a.emax + code) * 2 + c) * a.lp + j;
         if (CG) load_aff_cg(T, a.table, a.table_points, ti);
         else load_aff(T, a.table, a.table_points, ti);

@@ -1,7 +1,10 @@
 // Per-kernel CUDA-event timing (see profiler.cuh).  A fixed pool of event
 // pairs is created by pcmm_profile_enable; each profiled launch takes the
 // next pair.  Not thread-safe: enable, run and read from one host thread.
+// Every launch is also wrapped in an NVTX range named after its kernel (a
+// no-op unless a tracing tool is attached).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <vector>
 
@@ -23,6 +26,7 @@ const char* const g_names[KID_COUNT] = {"plan", "table", "gather", "normalize",
 }  // namespace
 
 ProfScope::ProfScope(int kernel_id, cudaStream_t s) : slot(-1), stream(s) {
+    nvtxRangePushA(kernel_id >= 0 && kernel_id < KID_COUNT ? g_names[kernel_id] : "pcmm");
     if (!g_on || g_used >= (int)g_slots.size()) return;
     slot = g_used++;
     g_slots[slot].kid = kernel_id;
@@ -31,6 +35,7 @@ ProfScope::ProfScope(int kernel_id, cudaStream_t s) : slot(-1), stream(s) {
 
 ProfScope::~ProfScope() {
     if (slot >= 0) cudaEventRecord(g_slots[slot].stop, stream);
+    nvtxRangePop();
 }
 
 }  // namespace pcmm

@@ -17,7 +17,9 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libpcmm.so")
+# The in-tree library; PCMM_LIBRARY may name another build of the same
+# sources (for example one compiled with -DPCMM_DEBUG_BOUNDS).
+LIB_PATH = os.environ.get("PCMM_LIBRARY") or os.path.join(_HERE, "libpcmm.so")
 
 PCMM_AFF_WORDS = 32
 PCMM_JAC_WORDS = 48
