@@ -80,6 +80,14 @@ def test_decrypt_encrypted_bytes_ragged(dev):
     out = pcmm.decrypt(pr["sk"], ct, 300, 99, steps)
     want = np.where(pr["B"] <= 99, pr["B"].astype(np.int64), -1)
     assert (out.cpu().numpy() == want).all()
+    # The degenerate range [0, 0] (its own table: 32 baby steps), and an
+    # empty call, which launches nothing.
+    zero = pcmm.BabySteps.for_range(0, device=dev)
+    out = pcmm.decrypt(pr["sk"], ct, 300, 0, zero)
+    assert (out.cpu().numpy() == np.where(pr["B"] == 0, 0, -1)).all()
+    empty = torch.full((4,), 7, dtype=torch.int64, device=dev)
+    pcmm.decrypt(pr["sk"], ct, 0, 255, steps, out=empty)
+    assert (empty.cpu().numpy() == 7).all()
 
 
 def test_wrong_key_finds_nothing(dev):
