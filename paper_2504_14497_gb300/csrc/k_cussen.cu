@@ -108,10 +108,16 @@ extern "C" int pcmm_cussen_choose_k(int m, int n, int l, int w) {
     return best;
 }
 
+// Table items (warps) per pass: four full waves of the table kernel on a
+// 152-SM GB300 (4 blocks of 4 warps per SM), measured 3 ms per headline step
+// faster than 4096 items, as long as one pass's scratch and tables stay
+// within PASS_BYTES_CAP; never fewer than MIN_ITEMS items' worth of strips.
 #ifndef PCMM_TARGET_ITEMS
-#define PCMM_TARGET_ITEMS 4096
+#define PCMM_TARGET_ITEMS 9728
 #endif
 static const size_t TARGET_ITEMS = PCMM_TARGET_ITEMS;
+static const size_t MIN_ITEMS = 4096;
+static const size_t PASS_BYTES_CAP = (size_t)16 << 30;
 
 namespace {
 size_t default_strips(const Layout& L);
@@ -208,7 +214,11 @@ pcmm_status launch_exec(const Layout& L, const PlanPtrs& P, const uint32_t* ctB,
 }
 
 size_t default_strips(const Layout& L) {
-    size_t S = (TARGET_ITEMS + L.items_per_strip - 1) / L.items_per_strip;
+    const size_t ips = L.items_per_strip;
+    size_t S = (TARGET_ITEMS + ips - 1) / ips;
+    const size_t cap = PASS_BYTES_CAP / L.per_strip_bytes;
+    const size_t least = (MIN_ITEMS + ips - 1) / ips;
+    if (S > cap) S = cap > least ? cap : least;
     if (S > (size_t)L.nstrips) S = L.nstrips;
     return S < 1 ? 1 : S;
 }

@@ -2,7 +2,9 @@
 mirrored from its documented structure so that GPU tests can read the plan
 and the strip tables back (test infrastructure)."""
 NLEV = 4
-TARGET_ITEMS = 4096
+TARGET_ITEMS = 9728          # table items per pass (pass scratch capped at 16 GiB,
+MIN_ITEMS = 4096             # but never below MIN_ITEMS items' worth of strips)
+PASS_BYTES_CAP = 16 << 30
 
 
 def _a256(x):
@@ -45,7 +47,12 @@ def single_pass_table(L):
     holds every strip and the gather does not split (m 2 njb >= 12288
     warps): the tables follow the plan and the pass's per-item scratch."""
     assert L["m"] * 2 * L["njb"] >= 12288, "the gather would split: partial sums precede the pass"
-    S = min(L["nstrips"], -(-TARGET_ITEMS // L["items_per_strip"]))
+    ips = L["items_per_strip"]
+    per_strip = ips * L["item_u4"] * 16 + _a256(L["emax"] * 2 * L["lp"] * 64)
+    S = -(-TARGET_ITEMS // ips)
+    if S > PASS_BYTES_CAP // per_strip:
+        S = max(PASS_BYTES_CAP // per_strip, -(-MIN_ITEMS // ips))
+    S = min(L["nstrips"], S)
     assert S == L["nstrips"], "more than one pass"
     table = L["plan_bytes"] + _a256(S * L["items_per_strip"] * L["item_u4"] * 16)
     return table, S * L["emax"] * 2 * L["lp"]
