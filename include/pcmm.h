@@ -146,7 +146,8 @@ pcmm_status pcmm_bsgs_build(uint32_t baby, void *table, size_t table_bytes, pcmm
  * only).  0 <= mmax <= 2^62.  out: device int64[count], written.
  * Errors: PCMM_EINVAL (null or misaligned pointers, x = 0 or x >= q, mmax
  * out of range, baby outside [1, 2^24], no pcmm_init), PCMM_ENOMEM
- * (table_bytes too small), PCMM_ECUDA. */
+ * (table_bytes too small), PCMM_EUNSUPPORTED (mmax / baby >= 2^20: more
+ * than 2^20 giant steps per ciphertext; use a larger baby), PCMM_ECUDA. */
 pcmm_status pcmm_decrypt(const uint32_t *sk_host, const uint32_t *ct, size_t count, int64_t mmax,
                          uint32_t baby, const void *table, size_t table_bytes, int64_t *out,
                          pcmm_stream_t stream);

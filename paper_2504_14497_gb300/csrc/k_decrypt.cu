@@ -33,6 +33,7 @@ namespace {
 
 constexpr int NAF_MAX = 260;          // digits of a 256-bit scalar in width-4 NAF (<= 257)
 constexpr uint32_t BABY_MAX = 1u << 24; // j < 2^24: three 8-bit comb windows
+constexpr uint64_t GIANT_MAX = 1u << 20; // giant steps per ciphertext at most
 
 struct Naf {
     int8_t d[NAF_MAX];  // d[i] in {0, +-1, +-3, +-5, +-7}, x = sum d[i] 2^i
@@ -320,6 +321,8 @@ extern "C" pcmm_status pcmm_decrypt(const uint32_t* sk_host, const uint32_t* ct,
         return PCMM_EINVAL;
     if (!valid_secret(sk_host)) return PCMM_EINVAL;
     if (table_bytes < pcmm_bsgs_bytes(baby)) return PCMM_ENOMEM;
+    // Each thread takes up to mmax / baby + 1 giant steps: bound the kernel's length.
+    if ((uint64_t)mmax / baby >= GIANT_MAX) return PCMM_EUNSUPPORTED;
     if (count == 0) return PCMM_OK;
     const uint4* gtab = comb_table_G();
     if (!gtab) return PCMM_EINVAL;

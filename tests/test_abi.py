@@ -100,6 +100,8 @@ def test_decrypt_host_validation_without_gpu(lib):
     assert dec(5, baby=0) == 1
     assert dec(5, baby=(1 << 24) + 1) == 1
     assert dec(5, nbytes=511) == 2
+    assert dec(5, mmax=(1 << 20) * 32, baby=32) == 5        # 2^20 + 1 giant steps
+    assert dec(5, mmax=1 << 50, baby=1 << 24, nbytes=8 << 25) == 5
     assert dec(q - 1, nbytes=511) == 2
     assert lib.pcmm_decrypt(None, d, 4, 100, 32, d, 512, d, None) == 1
 
