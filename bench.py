@@ -475,7 +475,11 @@ def run_batched(args, dist):
     if pcmm.workspace_status(batch.ws) != 0:
         raise RuntimeError("batched run reported a device error")
     # One plain launch per instance (plan + tables + gather each), same k.
-    wss = [pcmm.workspace(A.shape[0], A.shape[1], l, w, k, device=dev) for A, _, l, w, k in items]
+    # The launches run one after another on one stream, so they share one
+    # allocation; each gets exactly its default workspace size.
+    need = [pcmm.workspace_bytes(A.shape[0], A.shape[1], l, w, k) for A, _, l, w, k in items]
+    shared = torch.empty(max(need), dtype=torch.uint8, device=dev)
+    wss = [shared[:nb] for nb in need]
     outs = [torch.empty(48 * A.shape[0] * l, dtype=torch.int32, device=dev) for A, _, l, w, k in items]
 
     def plain():

@@ -8,8 +8,11 @@
 // (one launch, one block per strip) and ONE persistent kernel, so it can be
 // captured in a CUDA graph and replayed.
 //
-// The persistent kernel's warps pull tasks from a device-wide queue (an
-// atomic counter).  The schedule is a list of segments in round order: in
+// The persistent kernel's blocks pull four tasks at a time (one per warp)
+// from a device-wide queue (an atomic counter); when a strip's table tasks
+// come in multiples of four, the block's warps build one strip together and
+// share each field inversion.  The schedule is a list of segments in round
+// order (each padded to a multiple of four tasks): in
 // round r, the table-build tasks of every instance's r-th pass of strips,
 // then the gather tasks of those passes.  A task may wait (bounded spin) only
 // on tasks earlier in the queue:
@@ -17,10 +20,10 @@
 //     all gather tasks of pass r - 1 (they update the same outputs);
 //   * a table task of pass r waits for all gather tasks of pass r - 2 (the
 //     two table buffers of an instance alternate between passes).
-// Every task a warp waits on was pulled earlier by a warp that is running and
-// only waits on even earlier tasks, so the queue always progresses.  A wait
-// that exceeds its bound (about one second) sets a status bit and the warps
-// stop pulling tasks instead of hanging.
+// Every task a block waits on was pulled earlier by a block that is running
+// and only waits on even earlier tasks, so the queue always progresses.  A
+// wait that exceeds its bound (about one second) sets a status bit and the
+// blocks stop pulling tasks instead of hanging.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,6 +39,7 @@ namespace {
 
 constexpr int TASK_TABLE = 0, TASK_GATHER = 1;
 constexpr int BATCH_THREADS = 128;
+constexpr int BLOCK_TASKS = BATCH_THREADS / 32;   // tasks a block takes at once, one per warp
 
 struct Inst {
     const uint4* ctB;
@@ -79,53 +83,76 @@ __global__ void __launch_bounds__(BATCH_THREADS, PCMM_BATCH_MINBLOCKS) batched_k
                                                                 long long ntasks, BatchHeader* hdr,
                                                                 int* ctrs, uint4* scratch,
                                                                 size_t scratch_u4) {
-    const unsigned lane = threadIdx.x & 31u;
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const long long warp_id = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     uint4* my_scratch = scratch + (size_t)warp_id * scratch_u4;
+    __shared__ long long sh_t;
+    __shared__ int sh_seg, sh_go;
     for (;;) {
-        long long t = 0;
-        if (lane == 0) t = atomicAdd(&hdr->head, 1);
-        t = __shfl_sync(0xffffffffu, t, 0);
-        if (t >= ntasks) break;
-        if (*(volatile uint32_t*)&hdr->status & DEV_ERR_TIMEOUT) break;
-        // Segment holding task t (segments are sorted by start).
-        int lo = 0, hi = nsegs - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (segs[mid].start <= t) lo = mid; else hi = mid - 1;
+        // The block takes BLOCK_TASKS consecutive tasks of one segment (every
+        // segment starts at a multiple of BLOCK_TASKS), one per warp.  Every
+        // decision below that leads to a barrier or out of the loop is made
+        // by thread 0 and read from shared memory, so it is block-uniform.
+        if (threadIdx.x == 0) {
+            const long long t0 = atomicAdd(&hdr->head, BLOCK_TASKS);
+            int go = t0 < ntasks && !(*(volatile uint32_t*)&hdr->status & DEV_ERR_TIMEOUT);
+            int lo = 0;
+            if (go) {
+                // Segment holding task t0 (segments are sorted by start).
+                int hi = nsegs - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (segs[mid].start <= t0) lo = mid; else hi = mid - 1;
+                }
+                // Wait (bounded) for the tasks this segment depends on.
+                const Segment& sg = segs[lo];
+                const Inst& I = insts[sg.inst];
+                int* tdone = ctrs + I.ctr_base + 2 * sg.chunk;
+                const int sc = min(I.S, I.nstrips - sg.chunk * I.S);
+                if (sg.type == TASK_TABLE) {
+                    if (sg.chunk >= 2) go = wait_at_least(tdone - 4 + 1, I.m * 2 * I.njb, &hdr->status);
+                } else {
+                    go = wait_at_least(tdone, sc * 2 * I.njb, &hdr->status);
+                    if (go && sg.chunk > 0) go = wait_at_least(tdone - 2 + 1, I.m * 2 * I.njb, &hdr->status);
+                }
+            }
+            sh_t = t0;
+            sh_seg = lo;
+            sh_go = go;
         }
-        const Segment sg = segs[lo];
-        const long long item = t - sg.start;
+        __syncthreads();
+        const long long t0 = sh_t;
+        const int go = sh_go;
+        const Segment sg = segs[sh_seg];
+        __syncthreads();                      // shared values read before the next round
+        if (!go) break;
+        const long long item = t0 + warp - sg.start;
+        const bool real = item < sg.count;
         const Inst& I = insts[sg.inst];
         const int s0 = sg.chunk * I.S;
         const int sc = min(I.S, I.nstrips - s0);
         uint4* tbuf = I.tables + (size_t)(sg.chunk & 1) * 4 * I.table_points;
         int* tdone = ctrs + I.ctr_base + 2 * sg.chunk;
-        bool ok = true;
         if (sg.type == TASK_TABLE) {
-            if (sg.chunk >= 2 && lane == 0)
-                ok = wait_at_least(tdone - 4 + 1, I.m * 2 * I.njb, &hdr->status);
-            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
-            TableArgs ta;
-            ta.ctB = I.ctB;
-            ta.bshare = false;       // warps take tasks independently
-            ta.m = I.m; ta.n = I.n; ta.l = I.l; ta.w = I.w; ta.k = I.k;
-            ta.lp = I.lp; ta.njb = I.njb; ta.n1max = I.n1max; ta.l2max = I.l2max; ta.emax = I.emax;
-            ta.s0 = s0; ta.nstrips_chunk = sc;
-            ta.scratch = my_scratch;
-            ta.item_u4 = I.item_u4;
-            ta.table = tbuf;
-            ta.table_points = I.table_points;
-            table_item(ta, I.P, item, my_scratch);
-            __syncwarp();
-            __threadfence();
-            if (lane == 0) atomicAdd(tdone, 1);
-        } else {
-            if (lane == 0) {
-                ok = wait_at_least(tdone, sc * 2 * I.njb, &hdr->status);
-                if (ok && sg.chunk > 0) ok = wait_at_least(tdone - 2 + 1, I.m * 2 * I.njb, &hdr->status);
+            // A strip's items come in multiples of BLOCK_TASKS exactly when
+            // its item count is one; then the block's four items belong to one
+            // strip, follow one plan and share each inversion.
+            const int ips = 2 * I.njb;
+            const bool shared = (ips % BLOCK_TASKS) == 0;
+            if (real) {
+                TableArgs ta;
+                ta.ctB = I.ctB;
+                ta.bshare = shared;
+                ta.m = I.m; ta.n = I.n; ta.l = I.l; ta.w = I.w; ta.k = I.k;
+                ta.lp = I.lp; ta.njb = I.njb; ta.n1max = I.n1max; ta.l2max = I.l2max; ta.emax = I.emax;
+                ta.s0 = s0; ta.nstrips_chunk = sc;
+                ta.scratch = my_scratch;
+                ta.item_u4 = I.item_u4;
+                ta.table = tbuf;
+                ta.table_points = I.table_points;
+                table_item(ta, I.P, item, my_scratch);
             }
-            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+        } else if (real) {
             GatherArgs ga;
             ga.m = I.m; ga.l = I.l; ga.lp = I.lp; ga.njb = I.njb; ga.emax = I.emax;
             ga.parts = 1; ga.partial = nullptr;
@@ -135,9 +162,13 @@ __global__ void __launch_bounds__(BATCH_THREADS, PCMM_BATCH_MINBLOCKS) batched_k
             ga.table_points = I.table_points;
             ga.ctC = I.ctC;
             gather_item<true>(ga, I.P, item);
-            __syncwarp();
-            __threadfence();
-            if (lane == 0) atomicAdd(tdone + 1, 1);
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const long long left = sg.count - (t0 - sg.start);
+            const int done = (int)(left < BLOCK_TASKS ? left : BLOCK_TASKS);
+            atomicAdd(tdone + (sg.type == TASK_TABLE ? 0 : 1), done);
         }
     }
 }
@@ -153,14 +184,17 @@ struct HostLayout {
     int grid = 0;
 };
 
-// Strips per pass of one instance: at most max_strips (long gathers), and
-// few enough that the two table buffers stay near `table_budget` bytes.
 // Strips per pass of one instance.  An instance's passes run one after
 // another, so a pass should hold enough table warps to keep the queue busy
 // (PASS_ITEMS) while its two table buffers stay within 2 x BUFFER_CAP bytes:
 // at least min(64 strips, 256 MB for both buffers), raised to PASS_ITEMS
 // table items, capped by BUFFER_CAP per buffer and by max_strips when given.
-const size_t PASS_ITEMS = 1024;
+// The 64-instance batch measured 1172.4 ms at 1024 items, 1146.3 ms at 2048
+// and 1152.5 ms at 4096.
+#ifndef PCMM_BATCH_PASS_ITEMS
+#define PCMM_BATCH_PASS_ITEMS 2048
+#endif
+const size_t PASS_ITEMS = PCMM_BATCH_PASS_ITEMS;
 const size_t BUFFER_CAP = (size_t)2 << 30;
 
 int strips_per_pass(const Layout& L, int max_strips) {
@@ -238,13 +272,16 @@ pcmm_status build_layout(const pcmm_problem* probs, int count, int max_strips, i
                 sg.chunk = r;
                 sg.count = ph == 0 ? sc * 2 * I.njb : I.m * 2 * I.njb;
                 H.segs.push_back(sg);
-                t += sg.count;
+                // Segments start at multiples of BLOCK_TASKS: a block's tasks
+                // never straddle two segments (padding tasks do nothing).
+                t += (sg.count + BLOCK_TASKS - 1) / BLOCK_TASKS * BLOCK_TASKS;
             }
         }
     }
     H.ntasks = t;
-    // The queue head is a 32-bit counter that every warp bumps once past the end.
-    if (H.ntasks + (long long)grid * (BATCH_THREADS / 32) >= (1LL << 31)) return PCMM_EUNSUPPORTED;
+    // The queue head is a 32-bit counter that every block bumps by
+    // BLOCK_TASKS once past the end.
+    if (H.ntasks + (long long)grid * BLOCK_TASKS >= (1LL << 31)) return PCMM_EUNSUPPORTED;
     for (int i = 0; i < count; i++)
         for (int s = 0; s < H.insts[i].nstrips; s++) H.strip_map.push_back(make_int2(i, s));
     H.off_insts = off;   off = align256(off + sizeof(Inst) * count);

@@ -20,6 +20,7 @@ SPECS = [  # m, n, l, w, k
     (1, 17, 3, 2, 0),
     (70, 12, 1, 6, 2),
     (16, 16, 16, 4, 3),
+    (33, 25, 100, 5, 1),    # 8 table warps per strip: blocks of four share inversions
 ]
 
 
