@@ -224,9 +224,9 @@ pcmm_status pcmm_cussen16(const uint16_t *A, int m, int n, int w, const uint32_t
  *   aligned, >= pcmm_cussen_plan_bytes), clearing its status word (first 4
  *   bytes; read it with pcmm_workspace_status).
  * pcmm_cussen_exec_bytes: scratch bytes for one execution with l columns
- *   (the default pass: about 9728 table warps, four full waves on a 152-SM
- *   GB300, within 16 GiB but never fewer strips than 4096 warps' worth;
- *   any multiple of one strip's need works, larger means fewer passes).
+ *   (the default pass: whole waves of table warps on a 152-SM GB300, four
+ *   when a pass fits in 16 GiB, else as many as fit, at least one; any
+ *   multiple of one strip's need works, larger means fewer passes).
  * pcmm_cussen_execute: ctC = A Enc(B) using a plan built with the same m, n,
  *   w, k (not checked).  The plan is only read, so executions with their own
  *   scratch `ws` may run concurrently on different streams.

@@ -108,15 +108,17 @@ extern "C" int pcmm_cussen_choose_k(int m, int n, int l, int w) {
     return best;
 }
 
-// Table items (warps) per pass: four full waves of the table kernel on a
-// 152-SM GB300 (4 blocks of 4 warps per SM), measured 3 ms per headline step
-// faster than 4096 items, as long as one pass's scratch and tables stay
-// within PASS_BYTES_CAP; never fewer than MIN_ITEMS items' worth of strips.
-#ifndef PCMM_TARGET_ITEMS
-#define PCMM_TARGET_ITEMS 9728
+// Table items (warps) per pass come in whole waves of the table kernel on a
+// 152-SM GB300 (4 blocks of 4 warps per SM: 2432 items), so that only a
+// pass's last wave can run partly empty: four waves when one pass's scratch
+// and tables fit in PASS_BYTES_CAP, else as many whole waves as fit, at
+// least one.  Four waves measured 3 ms per headline step faster than 4096
+// items.
+#ifndef PCMM_TARGET_WAVES
+#define PCMM_TARGET_WAVES 4
 #endif
-static const size_t TARGET_ITEMS = PCMM_TARGET_ITEMS;
-static const size_t MIN_ITEMS = 4096;
+static const size_t WAVE_ITEMS = 152 * 4 * 4;
+static const size_t TARGET_WAVES = PCMM_TARGET_WAVES;
 static const size_t PASS_BYTES_CAP = (size_t)16 << 30;
 
 namespace {
@@ -215,10 +217,10 @@ pcmm_status launch_exec(const Layout& L, const PlanPtrs& P, const uint32_t* ctB,
 
 size_t default_strips(const Layout& L) {
     const size_t ips = L.items_per_strip;
-    size_t S = (TARGET_ITEMS + ips - 1) / ips;
-    const size_t cap = PASS_BYTES_CAP / L.per_strip_bytes;
-    const size_t least = (MIN_ITEMS + ips - 1) / ips;
-    if (S > cap) S = cap > least ? cap : least;
+    const size_t cap = PASS_BYTES_CAP / L.per_strip_bytes;   // strips within the byte cap
+    size_t waves = TARGET_WAVES;
+    while (waves > 1 && waves * WAVE_ITEMS / ips > cap) waves--;
+    size_t S = waves * WAVE_ITEMS / ips;                      // whole strips within the waves
     if (S > (size_t)L.nstrips) S = L.nstrips;
     return S < 1 ? 1 : S;
 }

@@ -2,8 +2,8 @@
 mirrored from its documented structure so that GPU tests can read the plan
 and the strip tables back (test infrastructure)."""
 NLEV = 4
-TARGET_ITEMS = 9728          # table items per pass (pass scratch capped at 16 GiB,
-MIN_ITEMS = 4096             # but never below MIN_ITEMS items' worth of strips)
+WAVE_ITEMS = 152 * 4 * 4     # one wave of the table kernel on a 152-SM GB300
+TARGET_WAVES = 4             # waves per pass, fewer when a pass exceeds 16 GiB
 PASS_BYTES_CAP = 16 << 30
 
 
@@ -49,10 +49,10 @@ def single_pass_table(L):
     assert L["m"] * 2 * L["njb"] >= 12288, "the gather would split: partial sums precede the pass"
     ips = L["items_per_strip"]
     per_strip = ips * L["item_u4"] * 16 + _a256(L["emax"] * 2 * L["lp"] * 64)
-    S = -(-TARGET_ITEMS // ips)
-    if S > PASS_BYTES_CAP // per_strip:
-        S = max(PASS_BYTES_CAP // per_strip, -(-MIN_ITEMS // ips))
-    S = min(L["nstrips"], S)
+    waves = TARGET_WAVES
+    while waves > 1 and waves * WAVE_ITEMS // ips > PASS_BYTES_CAP // per_strip:
+        waves -= 1
+    S = max(1, min(L["nstrips"], waves * WAVE_ITEMS // ips))
     assert S == L["nstrips"], "more than one pass"
     table = L["plan_bytes"] + _a256(S * L["items_per_strip"] * L["item_u4"] * 16)
     return table, S * L["emax"] * 2 * L["lp"]
