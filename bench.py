@@ -695,10 +695,16 @@ def run_sparse(args, dist):
             ms = timed(lambda: pcmm.cussen(A, ctB, l, w, k=k, ws=ws, out=out))
             if pcmm.workspace_status(ws) != 0:
                 raise RuntimeError(f"device status at w={w} rho={rho}")
+            # Per-kernel split of one more call (CUDA events around each launch).
+            pcmm.profile_enable(64)
+            pcmm.cussen(A, ctB, l, w, k=k, ws=ws, out=out)
+            prof = pcmm.profile_read()
+            pcmm.profile_enable(0)
             ops = counts.point_ops(counts.cussen_counts(A_h, w, k, l))
             dense_ms = ms if dense_ms is None else dense_ms
             rows.append({"w": w, "k": k, "density": rho, "nonzero_frac": float((A_h != 0).mean()),
-                         "cussen_ms": ms, "point_adds": ops, "point_adds_per_s": ops / (ms / 1e3),
+                         "cussen_ms": ms, "table_ms": prof["table"][0], "gather_ms": prof["gather"][0],
+                         "point_adds": ops, "point_adds_per_s": ops / (ms / 1e3),
                          "time_vs_first": ms / dense_ms})
             print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
         del ws
