@@ -125,3 +125,28 @@ def test_bounded_wait_gives_up_and_reports(dev):
     pcmm.test_wait(ctr, 2, status, out, 8)
     torch.cuda.synchronize()
     assert int(status.item()) == 0 and (out == 1).all()
+
+
+def test_batched_workload_config_sampled(dev):
+    # The batched workload's 64 shapes (m, n, l uniform in [32, 768], w in
+    # 1..8, the same shape seed as the benchmark) in one persistent launch
+    # with cost-model strip widths; sampled outputs of every instance against
+    # the closed form.
+    shapes = inputs.batched_shapes(inputs.SEED_BASE + 4, count=64)
+    items, probs = [], []
+    for i, (m, n, l, w) in enumerate(shapes):
+        pr = inputs.pcmm_problem(5200 + i, m, n, l, w)
+        items.append((torch.from_numpy(pr["A"]).to(dev), encrypt_gpu(dev, pr), l, w, 0))
+        probs.append(pr)
+    b = pcmm.Batch(items)
+    outs = b.run()
+    torch.cuda.synchronize()
+    assert pcmm.workspace_status(b.ws) == 0
+    rng = np.random.default_rng(64)
+    for (A, _, l, w, _), pr, out in zip(items, probs, outs):
+        m = A.shape[0]
+        got = _affine(out, m * l)
+        pairs = np.stack([rng.integers(0, m, 3), rng.integers(0, l, 3)], axis=1)
+        pairs = np.concatenate([pairs, [[0, 0], [m - 1, l - 1]]])
+        want = oracle.closed_form(pr["A"], pr["r"], pr["sk"], pr["B"], pairs=pairs)
+        assert mismatches(got[pairs[:, 0] * l + pairs[:, 1]], want) == 0, (m, A.shape[1], l, w)
