@@ -44,14 +44,17 @@ using namespace pcmm;
 using namespace pcmm::cussen;
 
 // Minimum resident blocks per SM requested from the compiler (its register
-// budget).  Measured on GB300: 5 blocks for the gather (96 registers) and 4
-// for the table build (128) beat the uncapped allocations despite a few
-// spilled registers.  Build-time tunables.
+// budget).  Measured on GB300: the gather is pipe-bound (5 blocks at 96
+// registers run as fast as 8); the table build waits on its scratch and
+// spill traffic, so more resident warps pay despite more spilling: table time
+// per headline step 46.3 ms at 4 blocks (128 registers), 45.1 at 5, 45.5 at
+// 6, 45.0 at 7 (72 registers), 47.3 at 8; per wide-value step 261.7, 259.3,
+// 252.7, 247.1 and 261.9 ms.  Build-time tunables.
 #ifndef PCMM_GATHER_MINBLOCKS
 #define PCMM_GATHER_MINBLOCKS 5
 #endif
 #ifndef PCMM_TABLE_MINBLOCKS
-#define PCMM_TABLE_MINBLOCKS 4
+#define PCMM_TABLE_MINBLOCKS 7
 #endif
 
 namespace {
@@ -109,15 +112,15 @@ extern "C" int pcmm_cussen_choose_k(int m, int n, int l, int w) {
 }
 
 // Table items (warps) per pass come in whole waves of the table kernel on a
-// 152-SM GB300 (4 blocks of 4 warps per SM: 2432 items), so that only a
+// 152-SM GB300 (PCMM_TABLE_MINBLOCKS blocks of 4 warps per SM), so that only a
 // pass's last wave can run partly empty: four waves when one pass's scratch
 // and tables fit in PASS_BYTES_CAP, else as many whole waves as fit, at
-// least one.  Four waves measured 3 ms per headline step faster than 4096
-// items.
+// least one.  Whole-wave passes measured 3 ms per headline step faster than
+// passes of 4096 items (at 4 blocks per SM).
 #ifndef PCMM_TARGET_WAVES
 #define PCMM_TARGET_WAVES 4
 #endif
-static const size_t WAVE_ITEMS = 152 * 4 * 4;
+static const size_t WAVE_ITEMS = 152 * PCMM_TABLE_MINBLOCKS * 4;
 static const size_t TARGET_WAVES = PCMM_TARGET_WAVES;
 static const size_t PASS_BYTES_CAP = (size_t)16 << 30;
 

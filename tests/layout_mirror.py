@@ -2,7 +2,7 @@
 mirrored from its documented structure so that GPU tests can read the plan
 and the strip tables back (test infrastructure)."""
 NLEV = 4
-WAVE_ITEMS = 152 * 4 * 4     # one wave of the table kernel on a 152-SM GB300
+WAVE_ITEMS = 152 * 7 * 4     # one wave of the table kernel on a 152-SM GB300 (7 blocks per SM)
 TARGET_WAVES = 4             # waves per pass, fewer when a pass exceeds 16 GiB
 PASS_BYTES_CAP = 16 << 30
 
