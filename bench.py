@@ -767,14 +767,14 @@ def run_decrypt(args, dist):
     got = out.cpu().numpy().reshape(m, l)
     if not (got == AB).all():
         raise RuntimeError(f"decryption differs from A B at {int((got != AB).sum())} outputs")
-    from oracle import oracle
-    sk_int = oracle.words_to_int(pr["sk"])
+    sk_int = int.from_bytes(np.asarray(pr["sk"], dtype="<u4").tobytes(), "little")
     prod = counts.decrypt_products(sk_int, AB, steps.baby)
     sm_max = clk.get("sm_max_mhz") or 2070.0
     peak = props.multi_processor_count * IMAD_PER_SM_PER_CLK * sm_max * 1e6
     imad_rate = count * prod * counts.IMAD_PER_PRODUCT / (ms / 1e3)
     cpu = None
     if not args.no_cpu_baseline:
+        from oracle import oracle
         ns = 512
         aos = pcmm.planar_to_ct(pcmm.to_host_words(ct), count)[:ns]
         t0 = time.perf_counter()
