@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--sparse-widths", default="8,4")
     ap.add_argument("--rates", default="10,20,50,100,200,500,1000,2000")
     ap.add_argument("--seconds", type=float, default=2.0, help="arrival window per rate (serving)")
+    ap.add_argument("--serving-inflight", type=int, default=8, help="batches in flight (serving)")
+    ap.add_argument("--serving-cols", type=int, default=256, help="columns per batch at most (serving)")
     return ap.parse_args()
 
 
@@ -810,11 +812,11 @@ def run_serving(args, dist):
 
     rng = np.random.default_rng(SEED + 3)
     st = inputs.streams(SEED + 3)
-    be = GpuBackend(f"cuda:{dist.local}", max_inflight=8)
+    be = GpuBackend(f"cuda:{dist.local}", max_inflight=args.serving_inflight)
     dev = be.device
     weights = {nm: (st["A"].integers(0, 16, size=shape, dtype=np.uint8), 4, 0)
                for nm, shape in SERVING_MODELS.items()}
-    srv_proto = dict(hbm_budget=40e9, max_inflight=8, max_batch_cols=256)
+    srv_proto = dict(hbm_budget=40e9, max_inflight=args.serving_inflight, max_batch_cols=args.serving_cols)
     sk = inputs.uniform_scalars(st["sk"], (1,))[0]
     tab = pcmm.keytable(pcmm.public_key(sk, device=dev), device=dev)
     pool = []                                   # (model, l, ct) encrypted inputs
