@@ -132,3 +132,22 @@ def test_layout_helpers_round_trip():
     r = rng.integers(0, 2**32, size=(6, 8), dtype=np.uint64).astype(np.uint32)
     rp = pcmm.scalars_to_planar(r)
     assert (rp[4 * 6 + 4 * 2: 4 * 6 + 4 * 2 + 4] == r[2, 4:8]).all()
+
+
+def test_workspace_sizes_follow_the_pass_rule(lib):
+    # Host-only: the default workspace is the plan plus one pass of whole
+    # waves of table warps (four when a pass fits in 16 GiB, fewer when not,
+    # at least one), capped at all strips; mirrored from the documented rule.
+    from tests.layout_mirror import PASS_BYTES_CAP, TARGET_WAVES, WAVE_ITEMS, _a256, layout
+
+    for (m, n, l, w, k) in [(1024, 1024, 256, 8, 1), (1024, 1024, 256, 4, 2), (1024, 1024, 256, 16, 1),
+                            (2048, 2048, 2048, 3, 2), (6144, 3000, 96, 12, 1), (1024, 700, 256, 1, 6)]:
+        L = layout(m, n, w, k, l)
+        assert m * 2 * L["njb"] >= 12288          # the gather does not split
+        ips = L["items_per_strip"]
+        per_strip = ips * L["item_u4"] * 16 + _a256(L["emax"] * 2 * L["lp"] * 64)
+        waves = TARGET_WAVES
+        while waves > 1 and waves * WAVE_ITEMS // ips > PASS_BYTES_CAP // per_strip:
+            waves -= 1
+        S = max(1, min(L["nstrips"], waves * WAVE_ITEMS // ips))
+        assert pcmm.workspace_bytes(m, n, l, w, k) == L["plan_bytes"] + S * per_strip, (m, n, l, w, k)
