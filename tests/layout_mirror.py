@@ -32,7 +32,7 @@ def layout(m, n, w, k, l=1):
     L["len"] = off; off = _a256(off + n * NLEV * 2)
     L["vN"] = off; off = _a256(off + n * L["l2max"] * 2)
     L["ptr"] = off; off = _a256(off + n * L["ptr_stride"] * 2)
-    off = _a256(off + (n * 256 if k > 1 else 0))
+    L["rank1"] = off; off = _a256(off + (n * 256 if k > 1 else 0))
     L["plan_bytes"] = off
     jac_ents = L["n1max"] + 2 * L["l2max"]
     aff_ents = L["l2max"] + (k * L["n1max"] + L["emax"] if k > 1 else 0)

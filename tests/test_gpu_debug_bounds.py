@@ -1,8 +1,8 @@
 """The debug-bounds build (-DPCMM_DEBUG_BOUNDS): on a clean plan its results
 equal the product library's and its status word stays 0; on a plan whose
-row ranks or tracking pointers were overwritten with indices one past the
-table they select from, it raises the bounds bit (8) in the status word and
-skips the access.  The corrupted indices are chosen so that even an
+row ranks, tracking pointers or (k = 2) tuple components were overwritten
+with indices one past the table they select from, it raises the bounds bit
+(8) in the status word and skips the access.  The corrupted indices are chosen so that even an
 unchecked access would stay inside the workspace.  Runs in a child process
 that loads the debug library through PCMM_LIBRARY."""
 import json
@@ -71,6 +71,35 @@ def bad_ptr(b):
     assert lens[3, 0] > 0 and lens[3, 1] <= L["l2max"]
     ptr[3, 0] = lens[3, 1]
 out["ptr"] = run(bad_ptr)
+
+# k = 2: a tuple component mapped one past its column's table (the column
+# tables of a strip are followed by more scratch of the same warp).
+m2, n2, l2, w2, k2 = 40, 6, 40, 4, 2
+pr2 = inputs.pcmm_problem(4343, m2, n2, l2, w2)
+ct2 = encrypt_gpu(dev, pr2)
+A2 = torch.from_numpy(pr2["A"]).to(dev)
+L2 = layout(m2, n2, w2, k2, l2)
+
+def bad_tuple(b):
+    lens = b[L2["len"]:L2["len"] + 2 * n2 * NLEV].view(np.uint16).reshape(n2, NLEV)
+    r1 = b[L2["rank1"]:L2["rank1"] + n2 * 256].reshape(n2, 256)
+    col = 1
+    v = int(pr2["A"][0, col])
+    v = v if v else int(pr2["A"][:, col].max())
+    assert v and lens[col, 0] <= L2["n1max"]
+    r1[col, v] = lens[col, 0]
+
+plan2 = pcmm.Plan(A2, w2, k2)
+torch.cuda.synchronize()
+b2 = plan2.buf.cpu().numpy()
+bad_tuple(b2)
+plan2.buf.copy_(torch.from_numpy(b2))
+run_affine(lambda: plan2.execute(ct2, l2), m2 * l2)
+out["tuple"] = [pcmm.workspace_status(plan2.buf), 0]
+want2 = oracle.closed_form(pr2["A"], pr2["r"], pr2["sk"], pr2["B"]).reshape(m2 * l2, 2, 16)
+ws2 = pcmm.workspace(m2, n2, l2, w2, k2, device=dev)
+got2 = run_affine(lambda: pcmm.cussen(A2, ct2, l2, w2, k=k2, ws=ws2), m2 * l2)
+out["clean_k2"] = [pcmm.workspace_status(ws2), mismatches(got2, want2)]
 print("RESULT " + json.dumps(out))
 """
 
@@ -89,3 +118,5 @@ def test_debug_bounds_flags_bad_plan_indices():
     assert r["product"] == 0
     assert r["rank"][0] & 8
     assert r["ptr"][0] & 8
+    assert r["tuple"][0] & 8
+    assert r["clean_k2"] == [0, 0]
