@@ -73,6 +73,7 @@ def _load():
                 "orc_scalar_mul": [u32p, u32p, u32p],
                 "orc_ladder": [ctypes.c_uint32, ci, u32p, u32p],
                 "orc_base_mul": [u32p, sz, u32p],
+                "orc_base_mul_comb": [u32p, sz, u32p],
                 "orc_keygen": [u32p, u32p],
                 "orc_encrypt": [u32p, u8p, u32p, sz, u32p],
                 "orc_decrypt": [u32p, u32p, sz, ctypes.c_int64, i64p],
@@ -197,6 +198,16 @@ def base_mul(scalars) -> np.ndarray:
     out = np.zeros((S.shape[0], 16), dtype=np.uint32)
     _check(_load().orc_base_mul(_p(S, ctypes.c_uint32), S.shape[0], _p(out, ctypes.c_uint32)),
            "base_mul")
+    return out
+
+
+def base_mul_comb(scalars) -> np.ndarray:
+    """base_mul by the fixed-base comb with shared inversions (the
+    evaluation closed_form uses)."""
+    S = _u32(scalars, (8,)).reshape(-1, 8)
+    out = np.zeros((S.shape[0], 16), dtype=np.uint32)
+    _check(_load().orc_base_mul_comb(_p(S, ctypes.c_uint32), S.shape[0], _p(out, ctypes.c_uint32)),
+           "base_mul_comb")
     return out
 
 

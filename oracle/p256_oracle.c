@@ -17,7 +17,10 @@
  *     chord-and-tangent group law with every exceptional case spelled out
  *     (Section 2.3: E(F_p) is an abelian group with identity infinity).
  *   - Scalar multiplication of small scalars by the Montgomery ladder
- *     (Algorithm 1); of 256-bit scalars by double-and-add.
+ *     (Algorithm 1); of 256-bit scalars by double-and-add; the closed
+ *     form's multiples of G by an 8-bit fixed-base comb whose additions of
+ *     one window share a single inversion (Montgomery's simultaneous
+ *     inversion), pinned against the bit-by-bit sum.
  *   - Schoolbook PC-MM (Section 3.1), Cussen PC-MM (Algorithms 2 and 3,
  *     N compression levels) and the closed form of the homomorphic linear
  *     combination (Eq. ahe_5_elgamal with H = xG).
@@ -268,19 +271,12 @@ static pt pt_dbl(const pt *a) {
     return r;
 }
 
-/* Addition with all exceptional cases: identity, P = Q, P = -Q. */
-static pt pt_add(const pt *a, const pt *b) {
-    if (a->inf) return *b;
-    if (b->inf) return *a;
-    if (u256_cmp(&a->x, &b->x) == 0) {
-        if (u256_cmp(&a->y, &b->y) == 0) return pt_dbl(a);
-        return pt_inf();                     /* b = -a */
-    }
-    u256 num, den, inv, lam, lam2, t, x3, y3;
+/* The chord step of the addition law for finite a, b with x_a != x_b,
+ * given dinv = 1 / (x_b - x_a): lambda = (y_b - y_a) dinv. */
+static pt pt_chord(const pt *a, const pt *b, const u256 *dinv) {
+    u256 num, lam, lam2, t, x3, y3;
     mod_sub(&FP, &num, &b->y, &a->y);
-    mod_sub(&FP, &den, &b->x, &a->x);
-    mont_inv(&FP, &inv, &den);
-    mont_mul(&FP, &lam, &num, &inv);
+    mont_mul(&FP, &lam, &num, dinv);
     mont_mul(&FP, &lam2, &lam, &lam);
     mod_sub(&FP, &x3, &lam2, &a->x);
     mod_sub(&FP, &x3, &x3, &b->x);           /* x3 = lambda^2 - x1 - x2 */
@@ -289,6 +285,20 @@ static pt pt_add(const pt *a, const pt *b) {
     mod_sub(&FP, &y3, &y3, &a->y);           /* y3 = lambda (x1 - x3) - y1 */
     pt r; r.x = x3; r.y = y3; r.inf = 0;
     return r;
+}
+
+/* Addition with all exceptional cases: identity, P = Q, P = -Q. */
+static pt pt_add(const pt *a, const pt *b) {
+    if (a->inf) return *b;
+    if (b->inf) return *a;
+    if (u256_cmp(&a->x, &b->x) == 0) {
+        if (u256_cmp(&a->y, &b->y) == 0) return pt_dbl(a);
+        return pt_inf();                     /* b = -a */
+    }
+    u256 den, inv;
+    mod_sub(&FP, &den, &b->x, &a->x);
+    mont_inv(&FP, &inv, &den);
+    return pt_chord(a, b, &inv);
 }
 
 /* Montgomery ladder, Algorithm 1: exactly t additions and t doublings for
@@ -333,6 +343,64 @@ static pt pt_mul_base(const u256 *s) {
     for (int i = 0; i < 256; i++)
         if (u256_bit(s, i)) acc = pt_add(&acc, &G_POW2[i]);
     return acc;
+}
+
+/* Fixed-base comb of G with 8-bit windows: COMB_G[i][v] = v 2^(8i) G for
+ * windows i = 0..31 and v = 0..255 (v = 0: the identity), built once by
+ * repeated addition of 2^(8i) G.  Then s G = sum_i COMB_G[i][byte_i(s)]. */
+static pt COMB_G[32][256];
+static int g_comb_ready = 0;
+
+static void ensure_comb(void) {
+    ensure_pow2();
+    if (g_comb_ready) return;
+    for (int i = 0; i < 32; i++) {
+        COMB_G[i][0] = pt_inf();
+        for (int v = 1; v < 256; v++) COMB_G[i][v] = pt_add(&COMB_G[i][v - 1], &G_POW2[8 * i]);
+    }
+    g_comb_ready = 1;
+}
+
+static int scalar_byte(const u256 *s, int i) { return (int)((s->w[i / 8] >> (8 * (i % 8))) & 0xff); }
+
+/* acc[p] = s[p] G for count scalars (COMB_CHUNK at most), window by window.
+ * The chord additions of one window share one field inversion (Montgomery's
+ * simultaneous inversion: invert the product of all denominators, then peel
+ * each 1 / (x_b - x_a) off with two multiplications); additions with the
+ * identity or with equal x coordinates go through pt_add. */
+#define COMB_CHUNK 256
+static void base_mul_comb(const u256 *s, size_t count, pt *acc) {
+    u256 den[COMB_CHUNK], pref[COMB_CHUNK];
+    int idx[COMB_CHUNK];
+    for (size_t p = 0; p < count; p++) acc[p] = pt_inf();
+    for (int i = 0; i < 32; i++) {
+        int nb = 0;
+        for (size_t p = 0; p < count; p++) {
+            const int v = scalar_byte(&s[p], i);
+            if (!v) continue;
+            const pt *T = &COMB_G[i][v];
+            if (acc[p].inf || u256_cmp(&acc[p].x, &T->x) == 0) {
+                acc[p] = pt_add(&acc[p], T);
+                continue;
+            }
+            mod_sub(&FP, &den[nb], &T->x, &acc[p].x);
+            pref[nb] = den[nb];
+            if (nb > 0) mont_mul(&FP, &pref[nb], &pref[nb - 1], &den[nb]);
+            idx[nb++] = (int)p;
+        }
+        if (nb == 0) continue;
+        u256 inv;                                  /* (den[0] ... den[t])^-1 */
+        mont_inv(&FP, &inv, &pref[nb - 1]);
+        for (int t = nb - 1; t >= 0; t--) {
+            u256 dinv = inv;
+            if (t > 0) {
+                mont_mul(&FP, &dinv, &inv, &pref[t - 1]);
+                mont_mul(&FP, &inv, &inv, &den[t]);
+            }
+            const int p = idx[t];
+            acc[p] = pt_chord(&acc[p], &COMB_G[i][scalar_byte(&s[p], i)], &dinv);
+        }
+    }
 }
 
 static int on_curve(const pt *a) {
@@ -480,6 +548,23 @@ int orc_base_mul(const uint32_t *s32, size_t count, uint32_t *out) {
         u256 s = u256_from_u32s(s32 + 8 * i);
         pt r = pt_mul_base(&s);
         pt_store(&r, out + 16 * i);
+    }
+    return 0;
+}
+
+/* The same products by the fixed-base comb (the evaluation the closed
+ * form uses); pinned against orc_base_mul. */
+int orc_base_mul_comb(const uint32_t *s32, size_t count, uint32_t *out) {
+    ensure_comb();
+    long long cnt = (long long)count;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long long c0 = 0; c0 < cnt; c0 += COMB_CHUNK) {
+        u256 s[COMB_CHUNK];
+        pt acc[COMB_CHUNK];
+        const size_t n0 = (size_t)(cnt - c0 < COMB_CHUNK ? cnt - c0 : COMB_CHUNK);
+        for (size_t t = 0; t < n0; t++) s[t] = u256_from_u32s(s32 + 8 * (c0 + t));
+        base_mul_comb(s, n0, acc);
+        for (size_t t = 0; t < n0; t++) pt_store(&acc[t], out + 16 * (c0 + t));
     }
     return 0;
 }
@@ -874,36 +959,55 @@ int orc_cussen(const uint16_t *A, int m, int n, int l, int w, int kstrip, int N,
 int orc_closed_form(const uint16_t *A, int m, int n, int l, const uint32_t *r32,
                     const uint32_t *sk32, const uint8_t *msg, const int32_t *ij, size_t npairs,
                     uint32_t *out) {
-    ensure_pow2();
+    ensure_comb();
     u256 sk = u256_from_u32s(sk32), skm;
     to_mont(&FQ, &skm, &sk);
-    long long np = (long long)npairs;
-    int bad = 0;
-#pragma omp parallel for schedule(dynamic, 4) reduction(|:bad)
-    for (long long p = 0; p < np; p++) {
-        int i = ij[2 * p], j = ij[2 * p + 1];
-        if (i < 0 || i >= m || j < 0 || j >= l) { bad |= 1; continue; }
-        u256 s1 = u256_small(0), s2 = u256_small(0);   /* Montgomery form mod q */
-        for (int k = 0; k < n; k++) {
-            u256 a = u256_small(A[(size_t)i * n + k]), am;
-            u256 r = u256_from_u32s(r32 + 8 * ((size_t)k * l + j)), rm;
-            u256 b = u256_small(msg[(size_t)k * l + j]), bm;
-            to_mont(&FQ, &am, &a);
-            to_mont(&FQ, &rm, &r);
-            to_mont(&FQ, &bm, &b);
-            u256 t1, t2;
-            mont_mul(&FQ, &t1, &am, &rm);              /* a r */
-            mod_add(&FQ, &s1, &s1, &t1);
-            mont_mul(&FQ, &t2, &rm, &skm);             /* r x */
-            mod_add(&FQ, &t2, &t2, &bm);               /* r x + b */
-            mont_mul(&FQ, &t2, &am, &t2);              /* a (r x + b) */
-            mod_add(&FQ, &s2, &s2, &t2);
-        }
-        from_mont(&FQ, &s1, &s1);
-        from_mont(&FQ, &s2, &s2);
-        pt c1 = pt_mul_base(&s1), c2 = pt_mul_base(&s2);
-        pt_store(&c1, out + 32 * p);
-        pt_store(&c2, out + 32 * p + 16);
+    const long long np = (long long)npairs, nl = (long long)n * l;
+    /* Per (k, j): r_kj and r_kj x + b_kj mod q, in Montgomery form. */
+    u256 *RM = (u256 *)malloc(sizeof(u256) * (size_t)nl);
+    u256 *TM = (u256 *)malloc(sizeof(u256) * (size_t)nl);
+    u256 *S = (u256 *)malloc(sizeof(u256) * (size_t)(2 * np + 1));
+    if (!RM || !TM || !S) { free(RM); free(TM); free(S); return -2; }
+#pragma omp parallel for schedule(static)
+    for (long long kj = 0; kj < nl; kj++) {
+        u256 r = u256_from_u32s(r32 + 8 * kj), b = u256_small(msg[kj]), bm;
+        to_mont(&FQ, &RM[kj], &r);
+        to_mont(&FQ, &bm, &b);
+        mont_mul(&FQ, &TM[kj], &RM[kj], &skm);           /* r x */
+        mod_add(&FQ, &TM[kj], &TM[kj], &bm);             /* r x + b */
     }
+    /* Per output: s1 = sum_k a_ik r_kj, s2 = sum_k a_ik (r_kj x + b_kj) mod q.
+     * For a plain a < q and a Montgomery-form y R, mont_mul(a, y R) = a y mod
+     * q, so the sums come out in plain form. */
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(|:bad)
+    for (long long p = 0; p < np; p++) {
+        const int i = ij[2 * p], j = ij[2 * p + 1];
+        u256 s1 = u256_small(0), s2 = u256_small(0);
+        if (i < 0 || i >= m || j < 0 || j >= l) { bad |= 1; S[2 * p] = s1; S[2 * p + 1] = s2; continue; }
+        for (int k = 0; k < n; k++) {
+            const u256 a = u256_small(A[(size_t)i * n + k]);
+            const size_t kj = (size_t)k * l + j;
+            u256 t;
+            mont_mul(&FQ, &t, &a, &RM[kj]);
+            mod_add(&FQ, &s1, &s1, &t);
+            mont_mul(&FQ, &t, &a, &TM[kj]);
+            mod_add(&FQ, &s2, &s2, &t);
+        }
+        S[2 * p] = s1;
+        S[2 * p + 1] = s2;
+    }
+    /* C1 = s1 G and C2 = s2 G: scalar 2p goes to words 32p, 2p + 1 to 32p + 16. */
+    const long long ns = 2 * np;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long long c0 = 0; c0 < ns; c0 += COMB_CHUNK) {
+        pt acc[COMB_CHUNK];
+        const size_t n0 = (size_t)(ns - c0 < COMB_CHUNK ? ns - c0 : COMB_CHUNK);
+        base_mul_comb(S + c0, n0, acc);
+        for (size_t t = 0; t < n0; t++) pt_store(&acc[t], out + 16 * (c0 + t));
+    }
+    free(RM);
+    free(TM);
+    free(S);
     return bad ? -1 : 0;
 }

@@ -105,3 +105,26 @@ def test_montgomery_ladder_matches_double_and_add():
             assert (O.ladder(k, 8, Pp) == O.scalar_mul(k, Pp)).all()
     with pytest.raises(O.OracleError):
         O.ladder(16, 4, pts[0])  # k needs 5 bits
+
+
+def test_comb_base_mul_matches_bitwise_sum_and_openssl():
+    # The closed form's fixed-base comb (8-bit windows, one shared inversion
+    # per window) against the bit-by-bit sum of 2^i G and OpenSSL: random
+    # scalars, scalars with zero bytes, and scalars >= q (s = q: the last
+    # window adds -acc, a vanishing sum).
+    rng = random.Random(21)
+    scal = [0, 1, 2, 255, 256, 2**248, 2**255, Q - 1, Q, Q + 1, Q - 2**248, 2**256 - 1, Q + 2**200]
+    scal += [rng.randrange(0, Q) & ~(0xFF << (8 * rng.randrange(32))) for _ in range(40)]
+    scal += [rng.randrange(0, 2**256) for _ in range(300)]
+    words = np.stack([O.int_to_words(s) for s in scal])
+    comb = O.base_mul_comb(words)
+    assert (comb == O.base_mul(words)).all()
+    for s, pt in zip(scal[:16], comb[:16]):
+        if s % Q:
+            assert (pt == _openssl_mul(s % Q)).all()
+        else:
+            assert (pt == 0).all()
+    # Chunks of 256 scalars: a ragged last chunk, and equal scalars in one
+    # chunk (identical accumulators share the window's inversion).
+    many = np.repeat(words[:7], 60, axis=0)
+    assert (O.base_mul_comb(many) == np.repeat(comb[:7], 60, axis=0)).all()
