@@ -268,7 +268,7 @@ def run_ours(args, dist):
     tab = pcmm.keytable(H, device=dev)
     msg = torch.from_numpy(base["B"].reshape(-1)).to(dev)
     rr = pcmm.to_device_words(pcmm.scalars_to_planar(base["r"]), dev)
-    ctB = pcmm.encrypt(tab, msg, rr)
+    ctB = pcmm.encrypt_table(tab, msg, rr)
     stream = torch.cuda.current_stream()
     runs = []
     for w in widths:
@@ -448,7 +448,7 @@ def run_batched(args, dist):
         A_h = st["A"].integers(0, 1 << w, size=(m, n), dtype=np.uint8)
         msg = st["B"].integers(0, 256, size=(n * l,), dtype=np.uint8)
         r = inputs.uniform_scalars(st["r"], (n * l,))
-        ctB = pcmm.encrypt(tab, torch.from_numpy(msg).to(dev), pcmm.to_device_words(pcmm.scalars_to_planar(r), dev))
+        ctB = pcmm.encrypt_table(tab, torch.from_numpy(msg).to(dev), pcmm.to_device_words(pcmm.scalars_to_planar(r), dev))
         items.append((torch.from_numpy(A_h).to(dev), ctB, l, w, k))
         ops += counts.point_ops(counts.cussen_counts(A_h, w, k, l))
     t_tune = time.perf_counter() - t_tune
@@ -479,7 +479,7 @@ def run_batched(args, dist):
     # One plain launch per instance (plan + tables + gather each), same k.
     # The launches run one after another on one stream, so they share one
     # allocation; each gets exactly its default workspace size.
-    need = [pcmm.workspace_bytes(A.shape[0], A.shape[1], l, w, k) for A, _, l, w, k in items]
+    need = [pcmm.cussen_workspace_bytes(A.shape[0], A.shape[1], l, w, k) for A, _, l, w, k in items]
     shared = torch.empty(max(need), dtype=torch.uint8, device=dev)
     wss = [shared[:nb] for nb in need]
     outs = [torch.empty(48 * A.shape[0] * l, dtype=torch.int32, device=dev) for A, _, l, w, k in items]
@@ -548,7 +548,7 @@ def run_sweep(args, dist):
     for n in (int(x) for x in args.sweep_n.split(",")):
         pr = inputs.pcmm_problem(seed, n, n, n, 1)
         tab = pcmm.keytable(pcmm.public_key(pr["sk"], device=dev), device=dev)
-        ctB = pcmm.encrypt(tab, torch.from_numpy(pr["B"].reshape(-1)).to(dev),
+        ctB = pcmm.encrypt_table(tab, torch.from_numpy(pr["B"].reshape(-1)).to(dev),
                            pcmm.to_device_words(pcmm.scalars_to_planar(pr["r"]), dev))
         out = torch.empty(48 * n * n, dtype=torch.int32, device=dev)
         for w in (int(x) for x in args.sweep_widths.split(",")):
@@ -605,7 +605,7 @@ def run_vector(args, dist):
     L = int(args.vector_scalars)
     pr = inputs.pcmm_problem(seed, 1, 1, L, 1)
     tab = pcmm.keytable(pcmm.public_key(pr["sk"], device=dev), device=dev)
-    ctB = pcmm.encrypt(tab, torch.from_numpy(pr["B"].reshape(-1)).to(dev),
+    ctB = pcmm.encrypt_table(tab, torch.from_numpy(pr["B"].reshape(-1)).to(dev),
                        pcmm.to_device_words(pcmm.scalars_to_planar(pr["r"]), dev))
     cur = torch.cuda.current_stream()
 
@@ -667,7 +667,7 @@ def run_sparse(args, dist):
     m, n, l = 1024, 1024, 256
     pr = inputs.pcmm_problem(SEED, 1, n, l, 1)
     tab = pcmm.keytable(pcmm.public_key(pr["sk"], device=dev), device=dev)
-    ctB = pcmm.encrypt(tab, torch.from_numpy(pr["B"].reshape(-1)).to(dev),
+    ctB = pcmm.encrypt_table(tab, torch.from_numpy(pr["B"].reshape(-1)).to(dev),
                        pcmm.to_device_words(pcmm.scalars_to_planar(pr["r"]), dev))
     out = torch.empty(48 * m * l, dtype=torch.int32, device=dev)
     cur = torch.cuda.current_stream()
@@ -738,7 +738,7 @@ def run_decrypt(args, dist):
     m, n, l, w = 1024, 1024, 256, 8
     pr = inputs.pcmm_problem(SEED, m, n, l, w)
     tab = pcmm.keytable(pcmm.public_key(pr["sk"], device=dev), device=dev)
-    ctB = pcmm.encrypt(tab, torch.from_numpy(pr["B"].reshape(-1)).to(dev),
+    ctB = pcmm.encrypt_table(tab, torch.from_numpy(pr["B"].reshape(-1)).to(dev),
                        pcmm.to_device_words(pcmm.scalars_to_planar(pr["r"]), dev))
     A = torch.from_numpy(pr["A"]).to(dev)
     ct = pcmm.normalize(pcmm.cussen(A, ctB, l, w), m * l)
@@ -825,7 +825,7 @@ def run_serving(args, dist):
             l = int(rng.integers(1, 65))
             msg = st["B"].integers(0, 256, size=(n * l,), dtype=np.uint8)
             r = inputs.uniform_scalars(st["r"], (n * l,))
-            ct = pcmm.encrypt(tab, torch.from_numpy(msg).to(dev),
+            ct = pcmm.encrypt_table(tab, torch.from_numpy(msg).to(dev),
                               pcmm.to_device_words(pcmm.scalars_to_planar(r), dev))
             pool.append((nm, l, ct))
     torch.cuda.synchronize()

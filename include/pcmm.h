@@ -96,15 +96,35 @@ size_t pcmm_keytable_bytes(void);
  * Errors: PCMM_EINVAL (null pointer, H not reduced or infinity). */
 pcmm_status pcmm_keytable(const uint32_t *H_host, void *keytable, pcmm_stream_t stream);
 
-/* Encrypts count messages.
- * keytable: device, from pcmm_keytable (read only).
+/* Bytes of the workspace of pcmm_encrypt: a 256-byte header naming the
+ * public key whose comb table follows, then that table. */
+size_t pcmm_encrypt_workspace_bytes(void);
+
+/* Encrypts count messages under the public key H (Section 2.4:
+ * Enc(b) = (rG, rH + bG), r drawn from [1, q-1] by the caller).
+ * H_host: host, 16 words (x then y), canonical, on the curve, not infinity.
  * msg: device uint8[count].  r: device scalars (quad-planar, 8 * count
- * words); each r is used modulo q (Section 2.4 draws r from [1, q-1]).
+ * words); each r is used modulo q, and is not checked against [1, q-1].
  * ct: device, affine ciphertext array of count elements (32 * count words),
- * written canonical.  Requires pcmm_init on the current device.
- * Errors: PCMM_EINVAL (null pointers), PCMM_ECUDA. */
-pcmm_status pcmm_encrypt(const void *keytable, const uint8_t *msg, const uint32_t *r, size_t count,
-                         uint32_t *ct, pcmm_stream_t stream);
+ * written canonical.
+ * ws: device, 256-byte aligned, >= pcmm_encrypt_workspace_bytes() bytes.
+ * It caches the comb table of H: a call whose workspace already holds the
+ * table of the same H (from an earlier pcmm_encrypt on the same stream
+ * order) skips the table build.  Do not write to the workspace between such
+ * calls, or clear its first 4 bytes to force a rebuild.  count = 0 only
+ * builds (or keeps) the table.  Requires pcmm_init on the current device.
+ * Errors: PCMM_EINVAL (null or misaligned pointers, H not reduced or
+ * infinity, no pcmm_init), PCMM_ENOMEM (ws_bytes too small), PCMM_ECUDA. */
+pcmm_status pcmm_encrypt(const uint32_t *H_host, const uint8_t *msg, const uint32_t *r, size_t count,
+                         uint32_t *ct, void *ws, size_t ws_bytes, pcmm_stream_t stream);
+
+/* pcmm_encrypt with a key table built once by pcmm_keytable (for callers
+ * that keep the table of each key themselves).
+ * keytable: device, from pcmm_keytable (read only).  Other arguments as
+ * pcmm_encrypt.  Errors: PCMM_EINVAL (null pointers, no pcmm_init),
+ * PCMM_ECUDA. */
+pcmm_status pcmm_encrypt_table(const void *keytable, const uint8_t *msg, const uint32_t *r, size_t count,
+                               uint32_t *ct, pcmm_stream_t stream);
 
 /* Multiplies the generator by count scalars: points[i] = s_i G (KeyGen,
  * Section 2.4: the public key is H = x G for the secret key x).
@@ -183,6 +203,27 @@ int pcmm_cussen_choose_k(int m, int n, int l, int w);
  * more strips per pass. */
 size_t pcmm_cussen_workspace_bytes(int m, int n, int l, int w, int k);
 
+/* Workspace bytes of one operation, by operation code:
+ *   PCMM_OP_ENCRYPT     pcmm_encrypt (independent of the sizes);
+ *   PCMM_OP_SCHOOLBOOK  pcmm_schoolbook(16): 0, it takes no workspace;
+ *   PCMM_OP_CUSSEN      pcmm_cussen / pcmm_cussen16 (k = 0: cost model);
+ *   PCMM_OP_NORMALIZE   pcmm_normalize of m * l ciphertexts: 0;
+ *   PCMM_OP_CUSSEN_PLAN pcmm_cussen_plan (k = 0: cost model for l);
+ *   PCMM_OP_CUSSEN_EXEC pcmm_cussen_execute's default scratch (ditto).
+ * m x n is the plaintext matrix A, n x l the ciphertext matrix Enc(B), w
+ * the bit-width of A's entries (1..16) and k the strip width.  Returns
+ * PCMM_WS_INVALID for an unknown operation or invalid sizes (so 0 always
+ * means "no workspace needed").  Batched problems are sized by
+ * pcmm_batched_workspace_bytes, which takes the problem list. */
+#define PCMM_OP_ENCRYPT 0
+#define PCMM_OP_SCHOOLBOOK 1
+#define PCMM_OP_CUSSEN 2
+#define PCMM_OP_NORMALIZE 3
+#define PCMM_OP_CUSSEN_PLAN 4
+#define PCMM_OP_CUSSEN_EXEC 5
+#define PCMM_WS_INVALID ((size_t)-1)
+size_t pcmm_workspace_bytes(int op, int m, int n, int l, int w, int k);
+
 /* Cussen PC-MM (Algorithms 2 and 3).  Strip width k = 1 is Algorithm 3 as
  * printed: each column of A is compressed (sort, remove duplicates, take
  * differences; N = 4 iterations), the compressed values are multiplied by
@@ -253,10 +294,19 @@ pcmm_status pcmm_cussen_execute(const void *plan, int m, int n, int w, int k, co
  * the start of every call and everything else is written before it is read,
  * but calls that overlap on the GPU (for instance on two streams without an
  * ordering between them) race on the array and corrupt each other's results.
+ * status: NULL, or 4 bytes of device memory (or host memory; pinned keeps
+ * the call asynchronous) that receive, in stream order after the kernels,
+ * the status word pcmm_cussen would leave in its workspace (1: an entry of
+ * A >= 2^w, masked to w bits; 2: a plan size over its bound; 8: a plan index
+ * out of range, debug-bounds builds only).  Non-zero means the product is
+ * not A Enc(B).
+ * The library keeps device state (this array's address, the generator's
+ * comb table) per device for the life of the process: a cudaDeviceReset
+ * between calls is not supported.
  * Errors: PCMM_EUNSUPPORTED when the problem needs more than the 32 MiB
  * (nothing is launched then), otherwise as pcmm_cussen. */
 pcmm_status pcmm_cussen_static(const uint8_t *A, int m, int n, int w, const uint32_t *ctB, int l,
-                               uint32_t *ctC, int k, pcmm_stream_t stream);
+                               uint32_t *ctC, int k, uint32_t *status, pcmm_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * Batched PC-MM: many Cussen instances of different shapes and bit-widths
@@ -312,6 +362,20 @@ pcmm_status pcmm_batched_prepare(const pcmm_problem *probs, int count, int max_s
  * of ws, pcmm_workspace_status) is set and the results are invalid.
  * Errors: PCMM_EINVAL, PCMM_ECUDA. */
 pcmm_status pcmm_batched_run(const pcmm_batch_info *info, void *ws, pcmm_stream_t stream);
+
+/* Batched Cussen PC-MM in one call (the batched form of Algorithm 3 over
+ * many independent problems): pcmm_batched_prepare with the library's
+ * default pass sizes, then pcmm_batched_run, on one workspace.  The prepare
+ * step uploads the schedule and synchronises `stream`; callers that replay
+ * the same batch (for instance from a CUDA graph) should prepare once and
+ * call pcmm_batched_run instead.
+ * probs: host array of count problems (see pcmm_problem).
+ * ws: device, 256-byte aligned, >= pcmm_batched_workspace_bytes(probs,
+ * count, 0); its first 4 bytes are the status word of the whole batch.
+ * Errors: PCMM_EINVAL, PCMM_ENOMEM, PCMM_EUNSUPPORTED (a queue over 2^31
+ * tasks), PCMM_ECUDA. */
+pcmm_status pcmm_cussen_batched(const pcmm_problem *probs, int count, void *ws, size_t ws_bytes,
+                                pcmm_stream_t stream);
 
 /* Reads the status word of a pcmm_cussen workspace into *status_host after
  * synchronising `stream`.  0 means no kernel raised an error bit. */

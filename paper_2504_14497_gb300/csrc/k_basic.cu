@@ -48,6 +48,52 @@ __global__ void __launch_bounds__(128) comb_build_kernel(aff base, uint4* __rest
     store_aff(tab, COMB_POINTS, idx, out[0]);
 }
 
+// Header of an encryption workspace: a tag word, then the 16 words of the
+// point whose comb table follows.  The build below skips its work when the
+// header already names the requested point.
+constexpr uint32_t KEY_TAG = 0x4b455931u;
+constexpr size_t ENC_HDR_BYTES = 256;
+
+__device__ __forceinline__ bool header_names(const uint32_t* __restrict__ hdr, const aff& X) {
+    bool same = hdr[0] == KEY_TAG;
+#pragma unroll
+    for (int i = 0; i < 8; i++) same &= (hdr[1 + i] == X.x.v[i]) & (hdr[9 + i] == X.y.v[i]);
+    return same;
+}
+
+// comb_build_kernel unless the header already names `base`.  Every block
+// reads the header before the tag kernel (next in stream order) writes it.
+__global__ void __launch_bounds__(128) comb_build_cached_kernel(aff base, const uint32_t* __restrict__ hdr,
+                                                                uint4* __restrict__ tab) {
+    if (header_names(hdr, base)) return;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int win = idx / COMB_ENTRIES, v = idx % COMB_ENTRIES;
+    uint32_t s[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) s[i] = 0;
+    s[win >> 2] = (uint32_t)v << (8 * (win & 3));
+    jac R[1];
+    jac_mul_u256(R[0], base, s);
+    aff out[1];
+    warp_normalize_regs<1>(out, R);
+    store_aff(tab, COMB_POINTS, idx, out[0]);
+}
+
+// Clears the tag when the header names another point, so that a table left
+// half rebuilt by a call that failed after this point is never reused.
+__global__ void comb_untag_kernel(aff base, uint32_t* __restrict__ hdr) {
+    if (threadIdx.x == 0 && !header_names(hdr, base)) hdr[0] = 0;
+}
+
+__global__ void comb_tag_kernel(aff base, uint32_t* __restrict__ hdr) {
+    const int i = threadIdx.x;
+    if (i < 8) {
+        hdr[1 + i] = base.x.v[i];
+        hdr[9 + i] = base.y.v[i];
+    }
+    if (i == 0) hdr[0] = KEY_TAG;
+}
+
 // Enc(b) = (rG, rH + bG): 32 window lookups per base point.
 __global__ void __launch_bounds__(128) encrypt_kernel(const uint4* __restrict__ gtab,
                                                       const uint4* __restrict__ htab,
@@ -316,17 +362,22 @@ static bool reduced_below_p(const uint32_t* v) {
     return false;
 }
 
-extern "C" pcmm_status pcmm_keytable(const uint32_t* H_host, void* keytable, pcmm_stream_t stream) {
-    if (!H_host || !keytable || ((uintptr_t)keytable & 15u)) return PCMM_EINVAL;
+// Validates a host public key and copies it into an affine point.
+static pcmm_status key_from_host(const uint32_t* H_host, aff& H) {
+    if (!H_host) return PCMM_EINVAL;
     if (!reduced_below_p(H_host) || !reduced_below_p(H_host + 8)) return PCMM_EINVAL;
-    aff H;
     uint32_t z = 0;
     for (int i = 0; i < 8; i++) {
         H.x.v[i] = H_host[i];
         H.y.v[i] = H_host[8 + i];
         z |= H_host[i] | H_host[8 + i];
     }
-    if (!z) return PCMM_EINVAL;
+    return z ? PCMM_OK : PCMM_EINVAL;
+}
+
+extern "C" pcmm_status pcmm_keytable(const uint32_t* H_host, void* keytable, pcmm_stream_t stream) {
+    aff H;
+    if (!keytable || ((uintptr_t)keytable & 15u) || key_from_host(H_host, H) != PCMM_OK) return PCMM_EINVAL;
     {
         ProfScope ps(KID_COMB, (cudaStream_t)stream);
         comb_build_kernel<<<COMB_POINTS / 128, 128, 0, (cudaStream_t)stream>>>(H, (uint4*)keytable);
@@ -335,20 +386,52 @@ extern "C" pcmm_status pcmm_keytable(const uint32_t* H_host, void* keytable, pcm
     return PCMM_OK;
 }
 
-extern "C" pcmm_status pcmm_encrypt(const void* keytable, const uint8_t* msg, const uint32_t* r,
-                                    size_t count, uint32_t* ct, pcmm_stream_t stream) {
-    if (!keytable || !msg || !r || !ct) return PCMM_EINVAL;
-    if (count == 0) return PCMM_OK;
+static pcmm_status launch_encrypt(const void* keytable, const uint8_t* msg, const uint32_t* r, size_t count,
+                                  uint32_t* ct, cudaStream_t st) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return PCMM_ECUDA;
     if (dev < 0 || dev >= 64 || !g_ready[dev]) return PCMM_EINVAL;
     uint4* gtab = nullptr;
     if (cudaGetSymbolAddress((void**)&gtab, g_comb_G) != cudaSuccess) return PCMM_ECUDA;
-    ProfScope ps(KID_ENCRYPT, (cudaStream_t)stream);
-    encrypt_kernel<<<grid_for(count, 128), 128, 0, (cudaStream_t)stream>>>(
-        gtab, (const uint4*)keytable, msg, (const uint4*)r, count, (uint4*)ct);
+    ProfScope ps(KID_ENCRYPT, st);
+    encrypt_kernel<<<grid_for(count, 128), 128, 0, st>>>(gtab, (const uint4*)keytable, msg, (const uint4*)r,
+                                                         count, (uint4*)ct);
     PCMM_CUDA_CHECK_LAUNCH();
     return PCMM_OK;
+}
+
+extern "C" pcmm_status pcmm_encrypt_table(const void* keytable, const uint8_t* msg, const uint32_t* r,
+                                          size_t count, uint32_t* ct, pcmm_stream_t stream) {
+    if (!keytable || !msg || !r || !ct) return PCMM_EINVAL;
+    if (count == 0) return PCMM_OK;
+    return launch_encrypt(keytable, msg, r, count, ct, (cudaStream_t)stream);
+}
+
+extern "C" size_t pcmm_encrypt_workspace_bytes(void) { return ENC_HDR_BYTES + (size_t)COMB_POINTS * 64; }
+
+extern "C" pcmm_status pcmm_encrypt(const uint32_t* H_host, const uint8_t* msg, const uint32_t* r, size_t count,
+                                    uint32_t* ct, void* ws, size_t ws_bytes, pcmm_stream_t stream) {
+    aff H;
+    if (key_from_host(H_host, H) != PCMM_OK) return PCMM_EINVAL;
+    if (!msg || !r || !ct || !ws || ((uintptr_t)ws & 255u)) return PCMM_EINVAL;
+    if (ws_bytes < pcmm_encrypt_workspace_bytes()) return PCMM_ENOMEM;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PCMM_ECUDA;
+    if (dev < 0 || dev >= 64 || !g_ready[dev]) return PCMM_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t* hdr = (uint32_t*)ws;
+    uint4* tab = (uint4*)((uint8_t*)ws + ENC_HDR_BYTES);
+    comb_untag_kernel<<<1, 32, 0, st>>>(H, hdr);
+    PCMM_CUDA_CHECK_LAUNCH();
+    {
+        ProfScope ps(KID_COMB, st);
+        comb_build_cached_kernel<<<COMB_POINTS / 128, 128, 0, st>>>(H, hdr, tab);
+    }
+    PCMM_CUDA_CHECK_LAUNCH();
+    comb_tag_kernel<<<1, 32, 0, st>>>(H, hdr);
+    PCMM_CUDA_CHECK_LAUNCH();
+    if (count == 0) return PCMM_OK;
+    return launch_encrypt(tab, msg, r, count, ct, st);
 }
 
 extern "C" pcmm_status pcmm_base_mul(const uint32_t* scalars, size_t count, uint32_t* points,

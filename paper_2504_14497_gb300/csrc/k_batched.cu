@@ -399,3 +399,12 @@ extern "C" pcmm_status pcmm_batched_run(const pcmm_batch_info* info, void* ws, p
     PCMM_CUDA_CHECK_LAUNCH();
     return PCMM_OK;
 }
+
+extern "C" pcmm_status pcmm_cussen_batched(const pcmm_problem* probs, int count, void* ws, size_t ws_bytes,
+                                           pcmm_stream_t stream) {
+    if (!probs || count < 1 || !ws) return PCMM_EINVAL;
+    pcmm_batch_info info;
+    const pcmm_status rc = pcmm_batched_prepare(probs, count, 0, ws, ws_bytes, &info, stream);
+    if (rc != PCMM_OK) return rc;
+    return pcmm_batched_run(&info, ws, stream);
+}

@@ -288,6 +288,30 @@ extern "C" size_t pcmm_cussen_workspace_bytes(int m, int n, int l, int w, int k)
     return L.plan_bytes + default_exec_bytes(L);
 }
 
+extern "C" size_t pcmm_workspace_bytes(int op, int m, int n, int l, int w, int k) {
+    const bool shape_ok = m >= 1 && n >= 1 && l >= 1 && w >= 1 && w <= PCMM_MAX_W16;
+    size_t b = 0;
+    switch (op) {
+        case PCMM_OP_ENCRYPT:
+            return pcmm_encrypt_workspace_bytes();
+        case PCMM_OP_SCHOOLBOOK:
+        case PCMM_OP_NORMALIZE:
+            return shape_ok ? 0 : PCMM_WS_INVALID;
+        case PCMM_OP_CUSSEN:
+            b = pcmm_cussen_workspace_bytes(m, n, l, w, k);
+            break;
+        case PCMM_OP_CUSSEN_PLAN:
+            b = pcmm_cussen_plan_bytes(m, n, w, k ? k : pcmm_cussen_choose_k(m, n, l, w));
+            break;
+        case PCMM_OP_CUSSEN_EXEC:
+            b = pcmm_cussen_exec_bytes(m, n, l, w, k ? k : pcmm_cussen_choose_k(m, n, l, w));
+            break;
+        default:
+            return PCMM_WS_INVALID;
+    }
+    return (shape_ok && b) ? b : PCMM_WS_INVALID;
+}
+
 extern "C" pcmm_status pcmm_cussen(const uint8_t* A, int m, int n, int w, const uint32_t* ctB, int l,
                                    uint32_t* ctC, int k, void* ws, size_t ws_bytes,
                                    pcmm_stream_t stream) {

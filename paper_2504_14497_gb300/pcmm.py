@@ -28,10 +28,11 @@ PCMM_MAX_WK = 16       # strip code width w * k, bits
 # Names of every exported entry point, in the order of include/pcmm.h.
 EXPORTS = (
     "pcmm_version", "pcmm_status_string", "pcmm_init", "pcmm_keytable_bytes", "pcmm_keytable",
-    "pcmm_encrypt", "pcmm_base_mul", "pcmm_bsgs_default_baby", "pcmm_bsgs_bytes", "pcmm_bsgs_build",
+    "pcmm_encrypt_workspace_bytes", "pcmm_encrypt", "pcmm_encrypt_table", "pcmm_base_mul", "pcmm_bsgs_default_baby", "pcmm_bsgs_bytes", "pcmm_bsgs_build",
     "pcmm_decrypt", "pcmm_schoolbook", "pcmm_schoolbook16", "pcmm_cussen_choose_k",
-    "pcmm_cussen_workspace_bytes", "pcmm_cussen", "pcmm_cussen16", "pcmm_cussen_plan_bytes", "pcmm_cussen_plan", "pcmm_cussen_exec_bytes",
+    "pcmm_workspace_bytes", "pcmm_cussen_workspace_bytes", "pcmm_cussen", "pcmm_cussen16", "pcmm_cussen_plan_bytes", "pcmm_cussen_plan", "pcmm_cussen_exec_bytes",
     "pcmm_cussen_execute", "pcmm_cussen_static", "pcmm_batched_workspace_bytes", "pcmm_batched_prepare", "pcmm_batched_run",
+    "pcmm_cussen_batched",
     "pcmm_workspace_status", "pcmm_copy_columns", "pcmm_normalize", "pcmm_profile_enable",
     "pcmm_profile_read", "pcmm_kernel_count", "pcmm_kernel_name", "pcmm_test_wait", "pcmm_test_field",
     "pcmm_test_point",
@@ -63,7 +64,9 @@ def lib():
                 "pcmm_init": ([ci], ci),
                 "pcmm_keytable_bytes": ([], sz),
                 "pcmm_keytable": ([u32p, vp, vp], ci),
-                "pcmm_encrypt": ([vp, vp, vp, sz, vp, vp], ci),
+                "pcmm_encrypt_workspace_bytes": ([], sz),
+                "pcmm_encrypt": ([u32p, vp, vp, sz, vp, vp, sz, vp], ci),
+                "pcmm_encrypt_table": ([vp, vp, vp, sz, vp, vp], ci),
                 "pcmm_base_mul": ([vp, sz, vp, vp], ci),
                 "pcmm_bsgs_default_baby": ([ctypes.c_int64], ctypes.c_uint32),
                 "pcmm_bsgs_bytes": ([ctypes.c_uint32], sz),
@@ -72,6 +75,7 @@ def lib():
                 "pcmm_schoolbook": ([vp, ci, ci, ci, vp, ci, vp, vp], ci),
                 "pcmm_schoolbook16": ([vp, ci, ci, ci, vp, ci, vp, vp], ci),
                 "pcmm_cussen_choose_k": ([ci, ci, ci, ci], ci),
+                "pcmm_workspace_bytes": ([ci, ci, ci, ci, ci, ci], sz),
                 "pcmm_cussen_workspace_bytes": ([ci, ci, ci, ci, ci], sz),
                 "pcmm_cussen": ([vp, ci, ci, ci, vp, ci, vp, ci, vp, sz, vp], ci),
                 "pcmm_cussen16": ([vp, ci, ci, ci, vp, ci, vp, ci, vp, sz, vp], ci),
@@ -79,8 +83,12 @@ def lib():
                 "pcmm_cussen_plan": ([vp, ci, ci, ci, ci, vp, sz, vp], ci),
                 "pcmm_cussen_exec_bytes": ([ci, ci, ci, ci, ci], sz),
                 "pcmm_cussen_execute": ([vp, ci, ci, ci, ci, vp, ci, vp, vp, sz, vp], ci),
-                "pcmm_cussen_static": ([vp, ci, ci, ci, vp, ci, vp, ci, vp], ci),
+                "pcmm_cussen_static": ([vp, ci, ci, ci, vp, ci, vp, ci, vp, vp], ci),
                 "pcmm_workspace_status": ([vp, u32p, vp], ci),
+                "pcmm_batched_workspace_bytes": ([vp, ci, ci], sz),
+                "pcmm_batched_prepare": ([vp, ci, ci, vp, sz, vp, vp], ci),
+                "pcmm_batched_run": ([vp, vp, vp], ci),
+                "pcmm_cussen_batched": ([vp, ci, vp, sz, vp], ci),
                 "pcmm_copy_columns": ([vp, sz, sz, vp, sz, sz, sz, sz, vp], ci),
                 "pcmm_normalize": ([vp, sz, vp, vp], ci),
                 "pcmm_test_field": ([ci, vp, vp, vp, sz, vp], ci),
@@ -197,17 +205,41 @@ def keytable(H: np.ndarray, device="cuda", stream=None):
     return tab
 
 
-def encrypt(table, msg, r_planar, out=None, stream=None):
-    """msg: cuda uint8[count]; r_planar: cuda int32[8 * count] (quad-planar
-    scalars).  Returns the affine ciphertext array, cuda int32[32 * count]."""
+def encrypt_workspace_bytes() -> int:
+    return int(lib().pcmm_encrypt_workspace_bytes())
+
+
+def encrypt(H: np.ndarray, msg, r_planar, ws=None, out=None, stream=None):
+    """pcmm_encrypt: Enc(b) = (rG, rH + bG) under the public key H
+    (uint32[16], x then y, on the host).  msg: cuda uint8[count]; r_planar:
+    cuda int32[8 * count] (quad-planar scalars); ws: an optional cuda uint8
+    workspace of ``encrypt_workspace_bytes()`` that caches the comb table of
+    H between calls.  Returns the affine ciphertext array, cuda
+    int32[32 * count]."""
+    torch = _torch()
+    count = msg.numel()
+    if r_planar.numel() != 8 * count:
+        raise ValueError("r must hold 8 words per message")
+    H = np.ascontiguousarray(H, dtype=np.uint32)
+    if ws is None:
+        ws = torch.empty(encrypt_workspace_bytes(), dtype=torch.uint8, device=msg.device)
+    if out is None:
+        out = torch.empty(PCMM_AFF_WORDS * count, dtype=torch.int32, device=msg.device)
+    _check(lib().pcmm_encrypt(H.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), _ptr(msg), _ptr(r_planar),
+                              count, _ptr(out), _ptr(ws), ws.numel(), _stream(stream)), "pcmm_encrypt")
+    return out
+
+
+def encrypt_table(table, msg, r_planar, out=None, stream=None):
+    """pcmm_encrypt_table: ``encrypt`` with a key table from ``keytable``."""
     torch = _torch()
     count = msg.numel()
     if r_planar.numel() != 8 * count:
         raise ValueError("r must hold 8 words per message")
     if out is None:
         out = torch.empty(PCMM_AFF_WORDS * count, dtype=torch.int32, device=msg.device)
-    _check(lib().pcmm_encrypt(_ptr(table), _ptr(msg), _ptr(r_planar), count, _ptr(out),
-                              _stream(stream)), "pcmm_encrypt")
+    _check(lib().pcmm_encrypt_table(_ptr(table), _ptr(msg), _ptr(r_planar), count, _ptr(out),
+                                    _stream(stream)), "pcmm_encrypt_table")
     return out
 
 
@@ -314,13 +346,23 @@ def choose_k(m: int, n: int, l: int, w: int) -> int:
     return int(lib().pcmm_cussen_choose_k(m, n, l, w))
 
 
-def workspace_bytes(m: int, n: int, l: int, w: int, k: int = 0) -> int:
+OP_ENCRYPT, OP_SCHOOLBOOK, OP_CUSSEN, OP_NORMALIZE, OP_CUSSEN_PLAN, OP_CUSSEN_EXEC = range(6)
+WS_INVALID = (1 << (8 * ctypes.sizeof(ctypes.c_size_t))) - 1
+
+
+def workspace_bytes(op: int, m: int, n: int, l: int, w: int, k: int = 0) -> int:
+    """pcmm_workspace_bytes: workspace of one operation (OP_*); WS_INVALID
+    for invalid sizes or an unknown operation."""
+    return int(lib().pcmm_workspace_bytes(op, m, n, l, w, k))
+
+
+def cussen_workspace_bytes(m: int, n: int, l: int, w: int, k: int = 0) -> int:
     return int(lib().pcmm_cussen_workspace_bytes(m, n, l, w, k))
 
 
 def workspace(m: int, n: int, l: int, w: int, k: int = 0, device="cuda"):
     torch = _torch()
-    nb = workspace_bytes(m, n, l, w, k)
+    nb = cussen_workspace_bytes(m, n, l, w, k)
     if nb == 0:
         raise ValueError("invalid PC-MM shape")
     return torch.empty(nb, dtype=torch.uint8, device=device)
@@ -348,15 +390,18 @@ def cussen16(A, ctB, l: int, w: int, k: int = 0, ws=None, out=None, stream=None)
     return cussen(A, ctB, l, w, k=k, ws=ws, out=out, stream=stream)
 
 
-def cussen_static(A, ctB, l: int, w: int, k: int = 0, out=None, stream=None):
+def cussen_static(A, ctB, l: int, w: int, k: int = 0, out=None, status=None, stream=None):
     """Cussen PC-MM on the library's static device scratch (no allocation by
     the library; ``out`` may be passed in so that none happens here either).
+    ``status``: an optional cuda int32 tensor of at least one element that
+    receives the call's status word (non-zero: the product is invalid).
     Raises PcmmError with PCMM_EUNSUPPORTED when the problem does not fit."""
     torch = _torch()
     m, n = A.shape
     if out is None:
         out = torch.empty(PCMM_JAC_WORDS * m * l, dtype=torch.int32, device=A.device)
-    _check(lib().pcmm_cussen_static(_ptr(A), m, n, w, _ptr(ctB), l, _ptr(out), k, _stream(stream)),
+    sp = _ptr(status) if status is not None else ctypes.c_void_p(0)
+    _check(lib().pcmm_cussen_static(_ptr(A), m, n, w, _ptr(ctB), l, _ptr(out), k, sp, _stream(stream)),
            "pcmm_cussen_static")
     return out
 
@@ -383,13 +428,6 @@ class Batch:
     def __init__(self, items, max_strips: int = 0, stream=None):
         torch = _torch()
         L = lib()
-        L.pcmm_batched_workspace_bytes.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
-        L.pcmm_batched_workspace_bytes.restype = ctypes.c_size_t
-        L.pcmm_batched_prepare.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
-                                           ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p]
-        L.pcmm_batched_prepare.restype = ctypes.c_int
-        L.pcmm_batched_run.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
-        L.pcmm_batched_run.restype = ctypes.c_int
         self.items = list(items)
         n = len(self.items)
         self.probs = (Problem * n)()
@@ -412,6 +450,39 @@ class Batch:
         _check(lib().pcmm_batched_run(ctypes.byref(self.info), _ptr(self.ws), _stream(stream)),
                "pcmm_batched_run")
         return self.outs
+
+
+def problems(items):
+    """ctypes array of pcmm_problem for items of (A, ctB, l, w, k, ctC)."""
+    arr = (Problem * len(items))()
+    for i, (A, ctB, l, w, k, ctC) in enumerate(items):
+        m, n = A.shape
+        if A.element_size() != 1:
+            raise TypeError("batched problems take a uint8 A")
+        arr[i] = Problem(_ptr(A).value, m, n, w, _ptr(ctB).value, l, _ptr(ctC).value, k)
+    return arr
+
+
+def batched_workspace_bytes(probs, max_strips: int = 0) -> int:
+    return int(lib().pcmm_batched_workspace_bytes(ctypes.cast(probs, ctypes.c_void_p), len(probs),
+                                                  int(max_strips)))
+
+
+def cussen_batched(items, ws=None, stream=None):
+    """pcmm_cussen_batched: items of (A, ctB, l, w, k); returns the Jacobian
+    outputs (one prepare + run on one workspace)."""
+    torch = _torch()
+    outs = [torch.empty(PCMM_JAC_WORDS * A.shape[0] * l, dtype=torch.int32, device=A.device)
+            for A, _, l, _, _ in items]
+    probs = problems([tuple(it) + (o,) for it, o in zip(items, outs)])
+    nb = batched_workspace_bytes(probs)
+    if nb == 0:
+        raise ValueError("invalid batch")
+    if ws is None:
+        ws = torch.empty(nb, dtype=torch.uint8, device=items[0][0].device)
+    _check(lib().pcmm_cussen_batched(ctypes.cast(probs, ctypes.c_void_p), len(probs), _ptr(ws), ws.numel(),
+                                     _stream(stream)), "pcmm_cussen_batched")
+    return outs
 
 
 class Plan:

@@ -36,7 +36,7 @@ def encrypt_gpu(dev, pr, H=None):
     tab = pcmm.keytable(H, device=dev)
     msg = torch.from_numpy(np.ascontiguousarray(pr["B"]).reshape(-1)).to(dev)
     r = pcmm.to_device_words(pcmm.scalars_to_planar(pr["r"]), dev)
-    return pcmm.encrypt(tab, msg, r)
+    return pcmm.encrypt_table(tab, msg, r)
 
 
 def ct_from_aos(dev, ct_aos):

@@ -44,12 +44,12 @@ def test_version_and_status_strings(lib):
 
 def test_host_validation_without_gpu(lib):
     # Invalid shapes are rejected before any CUDA call.
-    assert pcmm.workspace_bytes(0, 4, 4, 4, 1) == 0
-    assert pcmm.workspace_bytes(4, 4, 4, 17, 1) == 0   # w > 16
-    assert pcmm.workspace_bytes(4, 4, 4, 9, 2) == 0    # w * k = 18 > 16
-    assert pcmm.workspace_bytes(4, 4, 4, 4, 5) == 0    # w * k = 20 > 16
-    assert pcmm.workspace_bytes(4, 4, 4, 4, 4) > 0
-    assert pcmm.workspace_bytes(4, 4, 4, 16, 1) > 0
+    assert pcmm.cussen_workspace_bytes(0, 4, 4, 4, 1) == 0
+    assert pcmm.cussen_workspace_bytes(4, 4, 4, 17, 1) == 0   # w > 16
+    assert pcmm.cussen_workspace_bytes(4, 4, 4, 9, 2) == 0    # w * k = 18 > 16
+    assert pcmm.cussen_workspace_bytes(4, 4, 4, 4, 5) == 0    # w * k = 20 > 16
+    assert pcmm.cussen_workspace_bytes(4, 4, 4, 4, 4) > 0
+    assert pcmm.cussen_workspace_bytes(4, 4, 4, 16, 1) > 0
     assert lib.pcmm_cussen(None, 4, 4, 4, None, 4, None, 1, None, 0, None) == 1
     assert lib.pcmm_cussen16(None, 4, 4, 12, None, 4, None, 1, None, 0, None) == 1
     assert lib.pcmm_schoolbook(None, 4, 4, 4, None, 4, None, None) == 1
@@ -150,4 +150,56 @@ def test_workspace_sizes_follow_the_pass_rule(lib):
         while waves > 1 and waves * WAVE_ITEMS // ips > PASS_BYTES_CAP // per_strip:
             waves -= 1
         S = max(1, min(L["nstrips"], waves * WAVE_ITEMS // ips))
-        assert pcmm.workspace_bytes(m, n, l, w, k) == L["plan_bytes"] + S * per_strip, (m, n, l, w, k)
+        assert pcmm.cussen_workspace_bytes(m, n, l, w, k) == L["plan_bytes"] + S * per_strip, (m, n, l, w, k)
+
+
+def test_op_workspace_query(lib):
+    # pcmm_workspace_bytes dispatches by operation; 0 means "none needed",
+    # PCMM_WS_INVALID an invalid request.
+    inval = pcmm.WS_INVALID
+    assert pcmm.workspace_bytes(pcmm.OP_ENCRYPT, 1, 1, 1, 1) == pcmm.encrypt_workspace_bytes()
+    assert pcmm.encrypt_workspace_bytes() == 256 + pcmm.keytable_bytes()
+    assert pcmm.workspace_bytes(pcmm.OP_SCHOOLBOOK, 16, 16, 16, 4) == 0
+    assert pcmm.workspace_bytes(pcmm.OP_NORMALIZE, 16, 1, 16, 4) == 0
+    assert pcmm.workspace_bytes(pcmm.OP_SCHOOLBOOK, 0, 16, 16, 4) == inval
+    for (m, n, l, w, k) in [(1024, 1024, 256, 8, 1), (1024, 1024, 256, 4, 0), (300, 70, 9, 12, 1)]:
+        assert pcmm.workspace_bytes(pcmm.OP_CUSSEN, m, n, l, w, k) == pcmm.cussen_workspace_bytes(m, n, l, w, k)
+        kk = k or pcmm.choose_k(m, n, l, w)
+        assert pcmm.workspace_bytes(pcmm.OP_CUSSEN_PLAN, m, n, l, w, k) == lib.pcmm_cussen_plan_bytes(m, n, w, kk)
+        assert pcmm.workspace_bytes(pcmm.OP_CUSSEN_EXEC, m, n, l, w, k) == lib.pcmm_cussen_exec_bytes(m, n, l, w, kk)
+        # plan + default scratch = the one-call workspace
+        assert (pcmm.workspace_bytes(pcmm.OP_CUSSEN_PLAN, m, n, l, w, k)
+                + pcmm.workspace_bytes(pcmm.OP_CUSSEN_EXEC, m, n, l, w, k)
+                == pcmm.workspace_bytes(pcmm.OP_CUSSEN, m, n, l, w, k))
+    assert pcmm.workspace_bytes(pcmm.OP_CUSSEN, 4, 4, 4, 17, 1) == inval
+    assert pcmm.workspace_bytes(pcmm.OP_CUSSEN, 4, 4, 4, 4, 5) == inval
+    assert pcmm.workspace_bytes(99, 4, 4, 4, 4, 1) == inval
+    assert pcmm.workspace_bytes(-1, 4, 4, 4, 4, 1) == inval
+
+
+def test_encrypt_and_batched_host_validation(lib):
+    # Arguments rejected before any CUDA call (dummy pointers never used).
+    d = ctypes.c_void_p(256)
+    H = (ctypes.c_uint32 * 16)(*([5] * 16))
+    nb = pcmm.encrypt_workspace_bytes()
+    assert lib.pcmm_encrypt(None, d, d, 4, d, d, nb, None) == 1
+    assert lib.pcmm_encrypt((ctypes.c_uint32 * 16)(), d, d, 4, d, d, nb, None) == 1   # infinity
+    Hbig = (ctypes.c_uint32 * 16)(*([0xFFFFFFFF] * 16))                                # not reduced
+    assert lib.pcmm_encrypt(Hbig, d, d, 4, d, d, nb, None) == 1
+    assert lib.pcmm_encrypt(H, None, d, 4, d, d, nb, None) == 1
+    assert lib.pcmm_encrypt(H, d, d, 4, d, ctypes.c_void_p(272), nb, None) == 1       # misaligned ws
+    assert lib.pcmm_encrypt(H, d, d, 4, d, d, nb - 1, None) == 2
+    assert lib.pcmm_encrypt_table(None, d, d, 4, d, None) == 1
+    assert lib.pcmm_cussen_batched(None, 1, d, 1 << 20, None) == 1
+    assert lib.pcmm_cussen_batched(d, 1, None, 1 << 20, None) == 1
+
+
+def test_static_scratch_holds_the_headline_problem():
+    # The allocation-free entry point's 32 MiB scratch holds the plan and one
+    # strip of the 1024 x 1024 x 256 product at w = 8 (documented limit).
+    from tests.layout_mirror import _a256, layout
+
+    L = layout(1024, 1024, 8, 1, 256)
+    assert 1024 * 2 * L["njb"] >= 12288          # the gather does not split
+    one_strip = L["items_per_strip"] * L["item_u4"] * 16 + _a256(L["emax"] * 2 * L["lp"] * 64)
+    assert L["plan_bytes"] + one_strip <= 32 << 20

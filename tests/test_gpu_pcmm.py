@@ -168,7 +168,7 @@ def test_chunked_passes_match_single_pass(dev):
     want = _want(pr)
     passes = 0
     for k in (1, 2):
-        full = pcmm.workspace_bytes(m, n, l, w, k)
+        full = pcmm.cussen_workspace_bytes(m, n, l, w, k)
         # Smaller workspaces hold fewer strips and force several passes.
         for nb in (full, full // 3, full // 8):
             ws = torch.empty(nb, dtype=torch.uint8, device=dev)
@@ -191,7 +191,7 @@ def test_split_gather_over_several_passes(dev):
     m, n, l, w = 16, 200, 8, 4
     pr, A, ctB = _problem(dev, 820, m, n, l, w)
     want = _want(pr)
-    full = pcmm.workspace_bytes(m, n, l, w, 1)
+    full = pcmm.cussen_workspace_bytes(m, n, l, w, 1)
     plan = pcmm.lib().pcmm_cussen_plan_bytes(m, n, w, 1)
     for nb in (full, plan + (full - plan) // 3, plan + (full - plan) // 7, plan + (full - plan) // 40):
         ws = torch.empty(nb, dtype=torch.uint8, device=dev)

@@ -29,7 +29,7 @@ def test_results_identical_alone_and_in_the_mix():
         l = int(rng.integers(1, 9))
         msg = s["B"].integers(0, 256, size=(n, l), dtype=np.uint8)
         r = inputs.uniform_scalars(s["r"], (n, l))
-        ct = pcmm.encrypt(tab, torch.from_numpy(msg.reshape(-1)).to(dev),
+        ct = pcmm.encrypt_table(tab, torch.from_numpy(msg.reshape(-1)).to(dev),
                           pcmm.to_device_words(pcmm.scalars_to_planar(r), dev))
         reqs.append(Request(i, nm, ct, l, arrival=0.0005 * (i // 6)))
         plain.append((msg, r))
