@@ -33,7 +33,6 @@ import numpy as np  # noqa: E402
 
 METRIC = "encrypted PC-MM ciphertext point-adds/s and % int/HBM roofline (bit-exact) vs plain"
 UNIT = "point-adds/s"
-IMAD_PER_SM_PER_CLK = 64      # 32-bit integer multiply-add lanes per SM per clock
 SEED = 2504144970 + 2         # the large single PC-MM workload
 
 
@@ -166,12 +165,14 @@ class ClockSampler:
 
 # -------------------------------------------------------------- workload
 
-def recorded_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu record in
-    profiles/, or None when the kernel's source has changed since."""
+def recorded_profile(kernel: str):
+    """The committed ncu record of `kernel` in profiles/ (a JSON block with
+    per-launch DRAM traffic scaled to the headline launch and the kernel's
+    instruction mix per unit of work), or None when the kernel's source has
+    changed since it was taken."""
     import glob
     import hashlib
-    for path in glob.glob(os.path.join(ROOT, "profiles", "traffic_*.md")):
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         text = open(path).read()
         if "```json" not in text:
             continue
@@ -182,8 +183,38 @@ def recorded_traffic(kernel: str):
         for f in rec["source_files"]:
             h.update(open(os.path.join(ROOT, f), "rb").read())
         if h.hexdigest() == rec["source_sha256"]:
-            return rec["traffic_bytes_per_launch"]
+            return rec
     return None
+
+
+def measure_peaks(dev, repeats: int = 5) -> dict:
+    """Measured integer-pipe peaks of this GPU (thread-level instructions per
+    second): independent mad.lo / mad.hi / mad.wide / add.cc-addc / add
+    streams over whole waves of all SMs, best of `repeats` CUDA-event timings
+    after a warm-up launch.  mad.wide.u32 is one 32 x 32 -> 64-bit limb
+    product, so its rate is the product peak."""
+    import torch
+
+    from paper_2504_14497_gb300 import pcmm
+    props = torch.cuda.get_device_properties(dev)
+    blocks = props.multi_processor_count * 4
+    sink = torch.zeros(1024, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for op, iters in (("mad_lo", 200000), ("mad_hi", 100000), ("mad_wide", 100000),
+                      ("add_carry", 200000), ("add", 200000)):
+        pcmm.peak_run(op, blocks, 2000, sink)
+        best = float("inf")
+        for _ in range(repeats):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ops = pcmm.peak_run(op, blocks, iters, sink)
+            e1.record(stream)
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        out[op] = ops / (best / 1e3)
+    out["sms"] = props.multi_processor_count
+    return out
 
 
 def _host_plaintext(A):
@@ -286,6 +317,12 @@ def run_ours(args, dist):
             pcmm.cussen(r["A"], ctB, l, r["w"], k=r["k"], ws=r["ws"], out=r["jac"])
             pcmm.normalize(r["jac"], m * l, out=r["aff"])
 
+    # Integer-pipe peaks (outside the timed region), with the clocks seen.
+    pclk = ClockSampler(dev_index)
+    pclk.start()
+    peaks = measure_peaks(dev)
+    peak_clk = pclk.stop()
+
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -319,26 +356,45 @@ def run_ours(args, dist):
     value = replica_rate(dist.world, ops_step, args.steps, total_ms)
     launches = sum(v[1] for v in prof.values())
 
-    # ---- roofline of the dominant kernel (integer multiply-add bound)
+    # ---- roofline of the dominant kernel, against the measured peaks:
+    # algorithmic limb products per second over the measured mad.wide rate
+    # (one product each), and the binding ALU pipe's issue rate (the
+    # kernel's ALU instructions per unit of work from its committed ncu
+    # record) over the measured add.cc / addc rate.
     props = torch.cuda.get_device_properties(dev)
-    sm_max = clk.get("sm_max_mhz") or 2070.0
-    peak = props.multi_processor_count * IMAD_PER_SM_PER_CLK * sm_max * 1e6
-    kern = {"gather": sum(counts.gather_imad(r["counts"]) for r in runs),
-            "table": sum(counts.table_imad(r["counts"]) for r in runs)}
-    dom = max(kern, key=lambda nm: prof[nm][0])
-    dom_ms, dom_launches = prof[dom]
-    achieved = kern[dom] * args.steps / (dom_ms / 1e3)
-    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved / 1e12,
-                "peak": peak / 1e12, "unit": "TIMAD/s", "frac": achieved / peak,
-                "traffic": recorded_traffic(dom) if (m, n, l) == (1024, 1024, 256) else None,
-                "launches": dom_launches,
-                "avg_launch_ms": dom_ms / max(dom_launches, 1),
-                "peak_basis": f"{props.multi_processor_count} SMs x {IMAD_PER_SM_PER_CLK} IMAD/clk x {sm_max:.0f} MHz"}
+    prod_peak = peaks["mad_wide"]
+    alu_peak = peaks["add_carry"]
+    prods = {"gather": sum(counts.gather_imad(r["counts"]) for r in runs) // counts.IMAD_PER_PRODUCT,
+             "table": sum(counts.table_imad(r["counts"]) for r in runs) // counts.IMAD_PER_PRODUCT}
+    units = {"gather": sum(r["counts"]["gather_madd"] for r in runs),
+             "table": sum(counts.point_ops(r["counts"]) - r["counts"]["gather_madd"] for r in runs)}
     kernels = {nm: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
                for nm, v in prof.items() if v[1]}
     for nm in ("gather", "table"):
-        if nm in kernels:
-            kernels[nm]["frac_imad_peak"] = kern[nm] * args.steps / (prof[nm][0] / 1e3) / peak
+        if nm not in kernels:
+            continue
+        sec = prof[nm][0] / 1e3
+        kernels[nm]["products_per_s"] = prods[nm] * args.steps / sec
+        kernels[nm]["frac_product_peak"] = kernels[nm]["products_per_s"] / prod_peak
+        rec = recorded_profile(nm)
+        if rec and rec.get("alu_warp_inst_per_unit"):
+            alu_rate = units[nm] * args.steps * rec["alu_warp_inst_per_unit"] * 32 / sec
+            kernels[nm]["alu_inst_per_s"] = alu_rate
+            kernels[nm]["frac_alu_peak"] = alu_rate / alu_peak
+    dom = max(("gather", "table"), key=lambda nm: prof[nm][0])
+    dom_ms, dom_launches = prof[dom]
+    rec = recorded_profile(dom) if (m, n, l) == (1024, 1024, 256) else None
+    roofline = {"bound": "alu", "kernel": dom, "achieved": kernels[dom]["products_per_s"] / 1e12,
+                "peak": prod_peak / 1e12, "unit": "T limb-products/s",
+                "frac": kernels[dom]["frac_product_peak"],
+                "traffic": rec.get("traffic_bytes_per_launch") if rec else None,
+                "launches": dom_launches, "avg_launch_ms": dom_ms / max(dom_launches, 1),
+                "peak_basis": "measured: mad.wide.u32 (one 32x32->64-bit product) microbenchmark over "
+                              f"{props.multi_processor_count} SMs in this run",
+                "alu_frac": kernels[dom].get("frac_alu_peak"),
+                "alu_peak": alu_peak / 1e12, "alu_unit": "T thread-inst/s (add.cc/addc, measured)",
+                "peaks_measured": {k: (v / 1e12 if k != "sms" else v) for k, v in peaks.items()},
+                "peaks_clocks": peak_clk}
 
     # ---- schoolbook on the same GPU (context: Cussen speed-up, w = 8 and 4)
     schoolbook = None
@@ -575,8 +631,8 @@ def run_sweep(args, dist):
         del ctB, out
         torch.cuda.empty_cache()
     clk = clocks.stop()
-    sm_max = clk.get("sm_max_mhz") or 2070.0
-    peak = props.multi_processor_count * IMAD_PER_SM_PER_CLK * sm_max * 1e6
+    # Measured product peak (mad.wide.u32 rate), two IMAD-equivalents each.
+    peak = measure_peaks(dev)["mad_wide"] * counts.IMAD_PER_PRODUCT
     for r in rows:
         r["imad_frac"] = r.pop("imad") / (r["cussen_ms"] / 1e3) / peak
     return {"workload": "sweep: square PC-MM A n x n (uniform w-bit) x Enc(B) n x n (8-bit messages), "
@@ -771,8 +827,7 @@ def run_decrypt(args, dist):
         raise RuntimeError(f"decryption differs from A B at {int((got != AB).sum())} outputs")
     sk_int = int.from_bytes(np.asarray(pr["sk"], dtype="<u4").tobytes(), "little")
     prod = counts.decrypt_products(sk_int, AB, steps.baby)
-    sm_max = clk.get("sm_max_mhz") or 2070.0
-    peak = props.multi_processor_count * IMAD_PER_SM_PER_CLK * sm_max * 1e6
+    peak = measure_peaks(dev)["mad_wide"] * counts.IMAD_PER_PRODUCT   # measured, 2 IMAD per product
     imad_rate = count * prod * counts.IMAD_PER_PRODUCT / (ms / 1e3)
     cpu = None
     if not args.no_cpu_baseline:

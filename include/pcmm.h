@@ -402,6 +402,27 @@ pcmm_status pcmm_copy_columns(uint32_t *dst, size_t dst_ld, size_t dst_col, cons
                               pcmm_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Integer-pipe throughput microbenchmark (the measured peaks of the roofline
+ * that bounds the PC-MM kernels; not part of the method).  Each of blocks x
+ * pcmm_peak_threads_per_block() threads runs eight independent chains of
+ * one instruction kind for `iters` iterations, pcmm_peak_ops_per_iter(op)
+ * instructions per iteration, so the rate is threads x iters x ops / time.
+ * op: PCMM_PEAK_MAD_LO (mad.lo.u32), PCMM_PEAK_MAD_HI (mad.hi.u32),
+ * PCMM_PEAK_MAD_WIDE (mad.wide.u32: one 32 x 32 -> 64-bit limb product),
+ * PCMM_PEAK_ADD_CARRY (add.cc / addc carry chains), PCMM_PEAK_ADD (add.u32).
+ * sink: device, 1024 words, practically never written.
+ * Errors: PCMM_EINVAL (unknown op, blocks or iters < 1, null sink), PCMM_ECUDA.
+ * ---------------------------------------------------------------------- */
+#define PCMM_PEAK_MAD_LO 0
+#define PCMM_PEAK_MAD_HI 1
+#define PCMM_PEAK_MAD_WIDE 2
+#define PCMM_PEAK_ADD_CARRY 3
+#define PCMM_PEAK_ADD 4
+int pcmm_peak_ops_per_iter(int op);
+int pcmm_peak_threads_per_block(void);
+pcmm_status pcmm_peak_run(int op, int blocks, int iters, uint32_t *sink, pcmm_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Per-kernel timing.  pcmm_profile_enable(capacity > 0) creates `capacity`
  * pairs of CUDA events; from then on every library kernel launch records a
  * start and a stop event on its own stream (until the pool is used up).

@@ -33,7 +33,8 @@ EXPORTS = (
     "pcmm_workspace_bytes", "pcmm_cussen_workspace_bytes", "pcmm_cussen", "pcmm_cussen16", "pcmm_cussen_plan_bytes", "pcmm_cussen_plan", "pcmm_cussen_exec_bytes",
     "pcmm_cussen_execute", "pcmm_cussen_static", "pcmm_batched_workspace_bytes", "pcmm_batched_prepare", "pcmm_batched_run",
     "pcmm_cussen_batched",
-    "pcmm_workspace_status", "pcmm_copy_columns", "pcmm_normalize", "pcmm_profile_enable",
+    "pcmm_workspace_status", "pcmm_copy_columns", "pcmm_normalize", "pcmm_peak_ops_per_iter",
+    "pcmm_peak_threads_per_block", "pcmm_peak_run", "pcmm_profile_enable",
     "pcmm_profile_read", "pcmm_kernel_count", "pcmm_kernel_name", "pcmm_test_wait", "pcmm_test_field",
     "pcmm_test_point",
 )
@@ -91,6 +92,9 @@ def lib():
                 "pcmm_cussen_batched": ([vp, ci, vp, sz, vp], ci),
                 "pcmm_copy_columns": ([vp, sz, sz, vp, sz, sz, sz, sz, vp], ci),
                 "pcmm_normalize": ([vp, sz, vp, vp], ci),
+                "pcmm_peak_ops_per_iter": ([ci], ci),
+                "pcmm_peak_threads_per_block": ([], ci),
+                "pcmm_peak_run": ([ci, ci, ci, vp, vp], ci),
                 "pcmm_test_field": ([ci, vp, vp, vp, sz, vp], ci),
                 "pcmm_test_point": ([ci, vp, vp, vp, vp, sz, vp], ci),
             }
@@ -534,6 +538,20 @@ def normalize(ct_jac, count: int, out=None, stream=None):
         out = torch.empty(PCMM_AFF_WORDS * count, dtype=torch.int32, device=ct_jac.device)
     _check(lib().pcmm_normalize(_ptr(ct_jac), count, _ptr(out), _stream(stream)), "pcmm_normalize")
     return out
+
+
+# ---------------------------------------------------------- measurement
+
+PEAK_OPS = {"mad_lo": 0, "mad_hi": 1, "mad_wide": 2, "add_carry": 3, "add": 4}
+
+
+def peak_run(op: str, blocks: int, iters: int, sink, stream=None) -> int:
+    """Launches the integer-pipe microbenchmark; returns the thread-level
+    instructions it executes."""
+    code = PEAK_OPS[op]
+    _check(lib().pcmm_peak_run(code, int(blocks), int(iters), _ptr(sink), _stream(stream)), "pcmm_peak_run")
+    return int(blocks) * int(lib().pcmm_peak_threads_per_block()) * int(iters) * int(
+        lib().pcmm_peak_ops_per_iter(code))
 
 
 # ------------------------------------------------------------- unit tests
