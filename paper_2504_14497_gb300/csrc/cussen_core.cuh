@@ -13,6 +13,12 @@ namespace pcmm {
 namespace cussen {
 
 constexpr int NLEV = PCMM_N_ITER;   // compression iterations N
+
+// Whether the gather's mixed addition inlines its field multiplications
+// (build-time switch; out of line by default).
+#ifndef PCMM_GATHER_INLINE
+#define PCMM_GATHER_INLINE false
+#endif
 constexpr uint16_t NO_RANK = 0xFFFFu;
 constexpr int PLAN_THREADS = 256;
 
@@ -939,7 +945,7 @@ __device__ __forceinline__ void gather_item(const GatherArgs& a, const PlanPtrs&
         const size_t ti = (((size_t)sl * a.emax + code) * 2 + c) * a.lp + j;
         if (CG) load_aff_cg(T, a.table, a.table_points, ti);
         else load_aff(T, a.table, a.table_points, ti);
-        jacz_madd(acc, T);
+        jacz_madd_t<PCMM_GATHER_INLINE>(acc, T);
     }
     if (j < a.l) {
         jac out;

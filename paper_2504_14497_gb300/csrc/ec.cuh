@@ -169,7 +169,9 @@ __device__ __forceinline__ void jac_from_jacz(jac& R, const jacz& P) {
     R.Z = fmul(P.ZZ, P.ZZZ);
 }
 
-__device__ __forceinline__ void jacz_madd(jacz& P, const aff& Q) {
+// INL: field multiplications inlined (true) or out of line (false).
+template <bool INL>
+__device__ __forceinline__ void jacz_madd_t(jacz& P, const aff& Q) {
     if (aff_is_inf(Q)) return;
     if (fe_is_zero(P.ZZ)) {
         P.X = Q.x;
@@ -179,8 +181,8 @@ __device__ __forceinline__ void jacz_madd(jacz& P, const aff& Q) {
         return;
     }
     fe t1, t2, t3, t4, x3;
-    t1 = fmul(P.ZZ, Q.x);            // U2
-    t2 = fmul(P.ZZZ, Q.y);           // S2
+    t1 = mul_t<INL>(P.ZZ, Q.x);            // U2
+    t2 = mul_t<INL>(P.ZZZ, Q.y);           // S2
     fe_sub(t1, t1, P.X);             // H
     fe_sub(t2, t2, P.Y);             // R
     if (fe_is_zero(t1)) {
@@ -194,19 +196,21 @@ __device__ __forceinline__ void jacz_madd(jacz& P, const aff& Q) {
         }
         return;
     }
-    t4 = fsqr(t1);                   // H^2
-    t3 = fmul(t4, t1);               // H^3
-    P.ZZ = fmul(P.ZZ, t4);           // ZZ3 = ZZ1 H^2
-    P.ZZZ = fmul(P.ZZZ, t3);         // ZZZ3 = ZZZ1 H^3
-    t4 = fmul(t4, P.X);              // X1 H^2
+    t4 = sqr_t<INL>(t1);                   // H^2
+    t3 = mul_t<INL>(t4, t1);               // H^3
+    P.ZZ = mul_t<INL>(P.ZZ, t4);           // ZZ3 = ZZ1 H^2
+    P.ZZZ = mul_t<INL>(P.ZZZ, t3);         // ZZZ3 = ZZZ1 H^3
+    t4 = mul_t<INL>(t4, P.X);              // X1 H^2
     fe_add(t1, t4, t4);              // 2 X1 H^2
-    x3 = fsqr(t2);                   // R^2
+    x3 = sqr_t<INL>(t2);                   // R^2
     fe_sub(x3, x3, t1);
     fe_sub(x3, x3, t3);              // X3 = R^2 - 2 X1 H^2 - H^3
     fe_sub(t4, t4, x3);              // X1 H^2 - X3
-    P.Y = fmulsub(t4, t2, t3, P.Y);  // Y3 = R (X1 H^2 - X3) - Y1 H^3
+    P.Y = mulsub_t<INL>(t4, t2, t3, P.Y);  // Y3 = R (X1 H^2 - X3) - Y1 H^3
     P.X = x3;
 }
+
+__device__ __forceinline__ void jacz_madd(jacz& P, const aff& Q) { jacz_madd_t<false>(P, Q); }
 
 // Doubling in (X, Y, ZZ, ZZZ) coordinates (dbl-2001-b with delta = ZZ): Z
 // would become 2 Y Z, so ZZ is multiplied by rr2 = 4 Y^2 and ZZZ by

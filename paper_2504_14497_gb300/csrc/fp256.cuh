@@ -635,7 +635,7 @@ static __device__ __noinline__ void fe_inv(fe& r, const fe& a) {
 // r = a b - c d (mod p) with a single reduction: the two 512-bit products
 // are subtracted, p 2^256 (= 0 mod p) is added back while the difference is
 // negative (once, or on a rare branch twice), then the sum is reduced.
-static __device__ __noinline__ fe fmulsub(fe a, fe b, fe c, fe d) {
+__device__ __forceinline__ fe fe_mulsub(const fe& a, const fe& b, const fe& c, const fe& d) {
     uint32_t u[16], v[16];
     mul_wide(u, a, b);
     mul_wide(v, c, d);
@@ -691,6 +691,34 @@ static __device__ __noinline__ fe fmulsub(fe a, fe b, fe c, fe d) {
     fe r;
     fe_reduce(r, u);
     return r;
+}
+
+static __device__ __noinline__ fe fmulsub(fe a, fe b, fe c, fe d) { return fe_mulsub(a, b, c, d); }
+
+// Multiplication, squaring and a b - c d either out of line (INL = false:
+// one shared copy of the code) or inlined at the call site (INL = true).
+template <bool INL>
+__device__ __forceinline__ fe mul_t(const fe& a, const fe& b) {
+    if (INL) {
+        fe r;
+        fe_mul(r, a, b);
+        return r;
+    }
+    return fmul(a, b);
+}
+template <bool INL>
+__device__ __forceinline__ fe sqr_t(const fe& a) {
+    if (INL) {
+        fe r;
+        fe_sqr(r, a);
+        return r;
+    }
+    return fsqr(a);
+}
+template <bool INL>
+__device__ __forceinline__ fe mulsub_t(const fe& a, const fe& b, const fe& c, const fe& d) {
+    if (INL) return fe_mulsub(a, b, c, d);
+    return fmulsub(a, b, c, d);
 }
 
 }  // namespace pcmm

@@ -39,12 +39,14 @@ __global__ void __launch_bounds__(PEAK_THREADS) peak_kernel(int op, int iters, u
     } else if (op == PCMM_PEAK_MAD_WIDE) {
         for (int it = 0; it < iters; it++) {
 #pragma unroll
-            // The multiplicand is the low word of the chain's previous
-            // value, so no product is loop-invariant (a fixed a[i] b would
-            // let the assembler hoist the multiply and leave 64-bit adds).
+            // Chains 2q and 2q + 1 feed each other: each product's
+            // multiplicand is the low word of the other chain's latest
+            // value (a fixed multiplicand would let the assembler hoist the
+            // product; one taken from the accumulator's own register pair
+            // measured at a third of the rate).
             for (int i = 0; i < 8; i++)
-                asm volatile("{\n\t.reg .b32 lo, hi;\n\tmov.b64 {lo, hi}, %0;\n\t"
-                             "mad.wide.u32 %0, lo, %1, %0;\n\t}" : "+l"(d[i]) : "r"(b));
+                asm volatile("{\n\t.reg .b32 lo, hi;\n\tmov.b64 {lo, hi}, %1;\n\t"
+                             "mad.wide.u32 %0, lo, %2, %0;\n\t}" : "+l"(d[i]) : "l"(d[i ^ 1]), "r"(b));
         }
     } else if (op == PCMM_PEAK_ADD_CARRY) {
         // Two independent 4-limb additions with carry per iteration:
