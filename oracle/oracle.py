@@ -80,6 +80,7 @@ def _load():
                 "orc_schoolbook": [u16p, ci, ci, ci, ci, u32p, u32p, ll],
                 "orc_cussen": [u16p, ci, ci, ci, ci, ci, ci, u32p, u32p, ll],
                 "orc_closed_form": [u16p, ci, ci, ci, u32p, u32p, u8p, i32p, sz, u32p],
+                "orc_strassen": [u16p, ci, ci, ci, ci, ci, u32p, u32p, ll],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -293,6 +294,20 @@ def cussen(A, ctB, w: int, k: int = 1, N: int = N_ITER):
     return out, dict(zip(COUNT_KEYS, list(cnt)))
 
 
+def strassen(A, ctB, w: int, levels: int):
+    """Strassen PC-MM (Section 3.1): `levels` recursion steps of seven block
+    products and 13 ciphertext block additions (m, n, l even at each step),
+    schoolbook products below.  Returns (ctC uint32[m, l, 2, 16], counts)
+    with recon_add = ciphertext block additions, accum_add = schoolbook
+    accumulations."""
+    A, ctB, m, n, l = _pcmm_args(A, ctB)
+    out = np.zeros((m, l, 2, 16), dtype=np.uint32)
+    cnt = (ctypes.c_longlong * 5)()
+    _check(_load().orc_strassen(_p(A, ctypes.c_uint16), m, n, l, w, levels, _p(ctB, ctypes.c_uint32),
+                                _p(out, ctypes.c_uint32), cnt), "strassen")
+    return out, dict(zip(COUNT_KEYS, list(cnt)))
+
+
 def closed_form(A, r, sk, msg, pairs=None) -> np.ndarray:
     """C_ij = ((sum_k a_ik r_kj) G, (sum_k a_ik (r_kj sk + b_kj)) G).
 
@@ -347,6 +362,20 @@ def pcmm_equiv_cussen(n: int, vec_equiv: float) -> float:
     """Square PC-MM (m = n = l): n*l vector-times-ciphertext products plus
     2*m*l*(n-1) accumulation additions."""
     return n * n * vec_equiv + 2 * n * n * (n - 1)
+
+
+def pcmm_equiv_strassen(n: int, t: int) -> int:
+    """Equivalent point additions of Strassen PC-MM of square n x n
+    matrices (n a power of two) recursed down to single entries (Section
+    3.1): 7^log2(n) plaintext-ciphertext products of two ECSMs each (2t
+    additions per ECSM, Section 3.3) plus 13 ciphertext block additions per
+    step of two points each, A(n) = 7 A(n/2) + 13 (n/2)^2."""
+    mults, adds, k = 1, 0, 1
+    while k < n:
+        adds = 7 * adds + 13 * k * k
+        mults *= 7
+        k *= 2
+    return mults * 2 * 2 * t + 2 * adds
 
 
 def pcmm_equiv_schoolbook(n: int, t: int) -> int:

@@ -1011,3 +1011,161 @@ int orc_closed_form(const uint16_t *A, int m, int n, int l, const uint32_t *r32,
     free(S);
     return bad ? -1 : 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Strassen PC-MM (Section 3.1)                                        */
+/* ------------------------------------------------------------------ */
+
+/* a P for a signed plaintext scalar a: |a| P by the ladder (Algorithm 1),
+ * negated when a < 0 (block differences of A make negative entries). */
+static pt signed_mul(int32_t a, const pt *P, orc_counts *cnt) {
+    if (a == 0 || P->inf) return pt_inf();
+    uint32_t u = a < 0 ? (uint32_t)(-(int64_t)a) : (uint32_t)a;
+    cnt->ecsm++;
+    pt r = ladder_counted(u, bitlen(u), P, cnt);
+    return a < 0 ? pt_neg(&r) : r;
+}
+
+/* r = x + s y for one ciphertext element (both points), s = +1 or -1; the
+ * additions of two finite points are counted as block additions. */
+static void ct_addsub(pt *r, const pt *x, const pt *y, int s, orc_counts *cnt) {
+    for (int c = 0; c < 2; c++) {
+        pt yy = s < 0 ? pt_neg(&y[c]) : y[c];
+        if (!x[c].inf && !yy.inf) cnt->recon_add++;
+        r[c] = pt_add(&x[c], &yy);
+    }
+}
+
+/* C = A B for a signed plaintext block A (m x n, leading dimension lda)
+ * and a ciphertext block B (n x l, ldb elements of two points), C (m x l,
+ * ldc).  While levels > 0 and m, n, l are even, one step of Strassen's
+ * algorithm: the seven block products
+ *   M1 = (A11 + A22)(B11 + B22)   M2 = (A21 + A22) B11
+ *   M3 = A11 (B12 - B22)          M4 = A22 (B21 - B11)
+ *   M5 = (A11 + A12) B22          M6 = (A21 - A11)(B11 + B12)
+ *   M7 = (A12 - A22)(B21 + B22)
+ * then C11 = M1 + M4 - M5 + M7, C12 = M3 + M5, C21 = M2 + M4,
+ * C22 = M1 - M2 + M3 + M6: 5 plaintext and 5 + 8 = 13 ciphertext block
+ * additions or subtractions.  Otherwise the schoolbook product (Section 3.1),
+ * one signed scalar multiplication per term and additions into C. */
+static void strassen_rec(const int32_t *A, int lda, const pt *B, int ldb, pt *C, int ldc, int m, int n, int l,
+                         int levels, orc_counts *cnt, int parallel) {
+    if (levels == 0 || (m & 1) || (n & 1) || (l & 1)) {
+        for (int i = 0; i < m; i++)
+            for (int j = 0; j < l; j++)
+                for (int c = 0; c < 2; c++) {
+                    pt acc = pt_inf();
+                    for (int k = 0; k < n; k++) {
+                        pt t = signed_mul(A[(size_t)i * lda + k], &B[2 * ((size_t)k * ldb + j) + c], cnt);
+                        if (!acc.inf && !t.inf) cnt->accum_add++;
+                        acc = pt_add(&acc, &t);
+                    }
+                    C[2 * ((size_t)i * ldc + j) + c] = acc;
+                }
+        return;
+    }
+    const int mh = m / 2, nh = n / 2, lh = l / 2;
+    const size_t sa = (size_t)mh * nh, sb = (size_t)nh * lh, sc = (size_t)mh * lh;
+    int32_t *S = (int32_t *)malloc(sizeof(int32_t) * 7 * sa);
+    pt *T = (pt *)malloc(sizeof(pt) * 2 * 7 * sb);
+    pt *M = (pt *)malloc(sizeof(pt) * 2 * 7 * sc);
+    for (int i = 0; i < mh; i++)
+        for (int k = 0; k < nh; k++) {
+            const int32_t a11 = A[(size_t)i * lda + k], a12 = A[(size_t)i * lda + nh + k];
+            const int32_t a21 = A[(size_t)(mh + i) * lda + k], a22 = A[(size_t)(mh + i) * lda + nh + k];
+            const size_t e = (size_t)i * nh + k;
+            S[0 * sa + e] = a11 + a22;
+            S[1 * sa + e] = a21 + a22;
+            S[2 * sa + e] = a11;
+            S[3 * sa + e] = a22;
+            S[4 * sa + e] = a11 + a12;
+            S[5 * sa + e] = a21 - a11;
+            S[6 * sa + e] = a12 - a22;
+        }
+    for (int k = 0; k < nh; k++)
+        for (int j = 0; j < lh; j++) {
+            const pt *b11 = &B[2 * ((size_t)k * ldb + j)], *b12 = &B[2 * ((size_t)k * ldb + lh + j)];
+            const pt *b21 = &B[2 * ((size_t)(nh + k) * ldb + j)], *b22 = &B[2 * ((size_t)(nh + k) * ldb + lh + j)];
+            const size_t e = 2 * ((size_t)k * lh + j);
+            ct_addsub(&T[2 * 0 * sb + e], b11, b22, +1, cnt);
+            T[2 * 1 * sb + e] = b11[0];
+            T[2 * 1 * sb + e + 1] = b11[1];
+            ct_addsub(&T[2 * 2 * sb + e], b12, b22, -1, cnt);
+            ct_addsub(&T[2 * 3 * sb + e], b21, b11, -1, cnt);
+            T[2 * 4 * sb + e] = b22[0];
+            T[2 * 4 * sb + e + 1] = b22[1];
+            ct_addsub(&T[2 * 5 * sb + e], b11, b12, +1, cnt);
+            ct_addsub(&T[2 * 6 * sb + e], b21, b22, +1, cnt);
+        }
+    if (parallel) {
+        orc_counts sub[7];
+        memset(sub, 0, sizeof sub);
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int q = 0; q < 7; q++)
+            strassen_rec(S + q * sa, nh, T + 2 * q * sb, lh, M + 2 * q * sc, lh, mh, nh, lh, levels - 1, &sub[q], 0);
+        for (int q = 0; q < 7; q++) {
+            cnt->ecsm += sub[q].ecsm; cnt->ecsm_dbl += sub[q].ecsm_dbl; cnt->ecsm_add += sub[q].ecsm_add;
+            cnt->recon_add += sub[q].recon_add; cnt->accum_add += sub[q].accum_add;
+        }
+    } else {
+        for (int q = 0; q < 7; q++)
+            strassen_rec(S + q * sa, nh, T + 2 * q * sb, lh, M + 2 * q * sc, lh, mh, nh, lh, levels - 1, cnt, 0);
+    }
+    for (int i = 0; i < mh; i++)
+        for (int j = 0; j < lh; j++) {
+            const size_t e = 2 * ((size_t)i * lh + j);
+            const pt *M1 = &M[0 * 2 * sc + e], *M2 = &M[1 * 2 * sc + e], *M3 = &M[2 * 2 * sc + e];
+            const pt *M4 = &M[3 * 2 * sc + e], *M5 = &M[4 * 2 * sc + e], *M6 = &M[5 * 2 * sc + e];
+            const pt *M7 = &M[6 * 2 * sc + e];
+            pt *c11 = &C[2 * ((size_t)i * ldc + j)], *c12 = &C[2 * ((size_t)i * ldc + lh + j)];
+            pt *c21 = &C[2 * ((size_t)(mh + i) * ldc + j)], *c22 = &C[2 * ((size_t)(mh + i) * ldc + lh + j)];
+            pt t[2];
+            ct_addsub(t, M1, M4, +1, cnt);
+            ct_addsub(t, t, M5, -1, cnt);
+            ct_addsub(c11, t, M7, +1, cnt);
+            ct_addsub(c12, M3, M5, +1, cnt);
+            ct_addsub(c21, M2, M4, +1, cnt);
+            ct_addsub(t, M1, M2, -1, cnt);
+            ct_addsub(t, t, M3, +1, cnt);
+            ct_addsub(c22, t, M6, +1, cnt);
+        }
+    free(S);
+    free(T);
+    free(M);
+}
+
+/* Strassen PC-MM of A (m x n, entries < 2^w) and Enc(B) (n x l), `levels`
+ * recursion steps (each needs the current m, n, l even), schoolbook below.
+ * counts: ecsm (and its ladder's doublings and additions), recon_add =
+ * ciphertext block additions/subtractions of two finite points, accum_add
+ * = schoolbook accumulations. */
+int orc_strassen(const uint16_t *A, int m, int n, int l, int w, int levels, const uint32_t *ctB,
+                 uint32_t *ctC, long long *counts) {
+    ensure_init();
+    if (m < 1 || n < 1 || l < 1 || w < 1 || w > 16 || levels < 0 || levels > 8) return -1;
+    const uint32_t amask = (1u << w) - 1u;
+    int32_t *Ai = (int32_t *)malloc(sizeof(int32_t) * (size_t)m * n);
+    pt *B = (pt *)malloc(sizeof(pt) * 2 * (size_t)n * l);
+    pt *C = (pt *)malloc(sizeof(pt) * 2 * (size_t)m * l);
+    int rc = 0;
+    if (!Ai || !B || !C) rc = -2;
+    for (size_t i = 0; rc == 0 && i < (size_t)m * n; i++) {
+        if (A[i] & ~amask) rc = -1;
+        Ai[i] = A[i];
+    }
+    if (rc == 0 && load_ct_matrix(B, ctB, (size_t)n * l)) rc = -1;
+    if (rc == 0) {
+        orc_counts cnt;
+        memset(&cnt, 0, sizeof cnt);
+        strassen_rec(Ai, n, B, l, C, l, m, n, l, levels, &cnt, 1);
+        store_ct_matrix(ctC, C, (size_t)m * l);
+        if (counts) {
+            counts[0] = cnt.ecsm; counts[1] = cnt.ecsm_dbl; counts[2] = cnt.ecsm_add;
+            counts[3] = cnt.recon_add; counts[4] = cnt.accum_add;
+        }
+    }
+    free(Ai);
+    free(B);
+    free(C);
+    return rc;
+}
