@@ -47,15 +47,19 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-schoolbook", action="store_true")
-    ap.add_argument("--workload", choices=["large", "serving", "batched", "sweep", "vector", "decrypt", "sparse"],
+    ap.add_argument("--workload", choices=["large", "serving", "batched", "sweep", "vector", "decrypt", "sparse",
+                                           "strassen"],
                     default="large",
                     help="large: the single large PC-MM (the headline line); serving: Poisson "
                          "request sweep of encrypted linear layers; batched: 64 uneven instances; "
                          "sweep: square PC-MM over n and w, Cussen beside schoolbook; vector: "
                          "plaintext vector times ciphertext scalars; decrypt: baby-step "
                          "giant-step decryption of the large w = 8 product's output; sparse: the "
-                         "large product with mostly-zero A")
+                         "large product with mostly-zero A; strassen: schoolbook, Strassen and Cussen "
+                         "on square products (the paper's comparison)")
     ap.add_argument("--sweep-n", default="128,256,512,1024,2048")
+    ap.add_argument("--strassen-n", default="128,256,512,1024")
+    ap.add_argument("--strassen-widths", default="4,8")
     ap.add_argument("--sweep-widths", default="1,2,3,4,5,6,7,8,12,16")
     ap.add_argument("--vector-n", default="8,16,32,64,128,256,512")
     ap.add_argument("--vector-widths", default="4,8,12,16")
@@ -641,6 +645,93 @@ def run_sweep(args, dist):
             "peak_imad_per_s": peak, "clocks": clk, "rows": rows, "n_gpus": 1, "data": "synthetic (seeded)"}
 
 
+def run_strassen(args, dist):
+    """The paper's comparison systems on the GPU (Sections 3.1 and 4.2):
+    square A n x n (uniform w-bit) times Enc(B) n x n, schoolbook,
+    Strassen PC-MM at every recursion depth from 1 to the one leaving 16 x 16
+    leaf blocks (at most 5), and Cussen (cost-model k), each timed as one
+    launch sequence with CUDA events (best of two after a warm-up); the
+    Strassen and Cussen outputs are checked equal after normalisation.  The
+    schoolbook is timed on a row slice scaled to n rows, as in the sweep."""
+    import torch
+
+    from paper_2504_14497_gb300 import build, counts, inputs, pcmm
+
+    build.build()
+    torch.cuda.set_device(dist.local)
+    dev = torch.device("cuda", dist.local)
+    pcmm.init(dist.local)
+    clocks = ClockSampler(dist.local)
+    clocks.start()
+    seed = 2504144970 + 7
+    cur = torch.cuda.current_stream()
+
+    def timed(fn, reps=2):
+        fn()
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(cur)
+            fn()
+            e1.record(cur)
+            e1.synchronize()
+            t = e0.elapsed_time(e1)
+            best = t if best is None else min(best, t)
+        return best
+
+    rows = []
+    for n in (int(x) for x in args.strassen_n.split(",")):
+        pr = inputs.pcmm_problem(seed, n, n, n, 1)
+        ctB = pcmm.encrypt(pcmm.public_key(pr["sk"], device=dev), torch.from_numpy(pr["B"].reshape(-1)).to(dev),
+                           pcmm.to_device_words(pcmm.scalars_to_planar(pr["r"]), dev))
+        out = torch.empty(48 * n * n, dtype=torch.int32, device=dev)
+        out2 = torch.empty_like(out)
+        for w in (int(x) for x in args.strassen_widths.split(",")):
+            A_h = inputs.plaintext_matrix(seed, n, n, w)
+            A = torch.from_numpy(A_h).to(dev)
+            k = pcmm.choose_k(n, n, n, w)
+            ws = pcmm.workspace(n, n, n, w, k, device=dev)
+            cu = timed(lambda: pcmm.cussen(A, ctB, n, w, k=k, ws=ws, out=out))
+            ref = pcmm.normalize(out, n * n)
+            del ws
+            ops_row = 2.0 * n * n * (1.5 * w + 1)
+            ms_rows = int(min(n, max(8, 4e9 // ops_row)))
+            sb = timed(lambda: pcmm.schoolbook(A[:ms_rows], ctB, n, w, out=out2), reps=1) * n / ms_rows
+            depths = {}
+            same = True
+            d = 1
+            while d <= 5 and (n >> d) >= 16:
+                wsb = torch.empty(pcmm.strassen_workspace_bytes(n, n, n, w, d), dtype=torch.uint8, device=dev)
+                ms = timed(lambda: pcmm.strassen(A, ctB, n, w, d, ws=wsb, out=out2), reps=1)
+                same &= bool(torch.equal(pcmm.normalize(out2, n * n), ref))
+                c = counts.strassen_counts(A_h, w, d, n)
+                depths[d] = {"ms": ms, "point_adds_per_s": counts.strassen_point_ops(c) / (ms / 1e3)}
+                del wsb
+                torch.cuda.empty_cache()
+                d += 1
+            best_d = min(depths, key=lambda x: depths[x]["ms"]) if depths else None
+            st_ms = depths[best_d]["ms"] if depths else None
+            row = {"n": n, "w": w, "cussen_ms": cu, "cussen_k": k, "schoolbook_ms": sb,
+                   "strassen": depths, "strassen_best_depth": best_d, "strassen_ms": st_ms,
+                   "speedup_cussen_vs_strassen": st_ms / cu if st_ms else None,
+                   "speedup_cussen_vs_schoolbook": sb / cu,
+                   "speedup_strassen_vs_schoolbook": sb / st_ms if st_ms else None,
+                   "paper_equiv_adds": {"schoolbook": 2 * n ** 3 * 2 * w + 2 * n * n * (n - 1),
+                                        "strassen": counts.strassen_equiv(n, w)},
+                   "outputs_identical": same}
+            rows.append(row)
+            print(json.dumps(row), file=sys.stderr, flush=True)
+            torch.cuda.empty_cache()
+        del ctB, out, out2
+        torch.cuda.empty_cache()
+    clk = clocks.stop()
+    return {"workload": "strassen: square PC-MM A n x n (uniform w-bit) x Enc(B) n x n (8-bit messages): "
+                        "schoolbook, Strassen PC-MM (depths 1..5, schoolbook leaves) and Cussen on one GPU",
+            "metric": "wall time per PC-MM and Cussen speed-up over Strassen and schoolbook", "unit": "ms",
+            "rows": rows, "clocks": clk, "n_gpus": 1, "data": "synthetic (seeded)"}
+
+
 def run_vector(args, dist):
     """Plaintext vector times ciphertext scalar (the paper's Sections 3.2 and
     4.2): a vector a of n t-bit entries times one ciphertext, giving n
@@ -962,6 +1053,8 @@ def main():
             out = run_decrypt(args, dist)
         elif args.workload == "sparse":
             out = run_sparse(args, dist)
+        elif args.workload == "strassen":
+            out = run_strassen(args, dist)
         else:
             out = run_ours(args, dist)
         if dist.rank == 0 and out is not None:

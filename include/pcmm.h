@@ -209,7 +209,8 @@ size_t pcmm_cussen_workspace_bytes(int m, int n, int l, int w, int k);
  *   PCMM_OP_CUSSEN      pcmm_cussen / pcmm_cussen16 (k = 0: cost model);
  *   PCMM_OP_NORMALIZE   pcmm_normalize of m * l ciphertexts: 0;
  *   PCMM_OP_CUSSEN_PLAN pcmm_cussen_plan (k = 0: cost model for l);
- *   PCMM_OP_CUSSEN_EXEC pcmm_cussen_execute's default scratch (ditto).
+ *   PCMM_OP_CUSSEN_EXEC pcmm_cussen_execute's default scratch (ditto);
+ *   PCMM_OP_STRASSEN    pcmm_strassen with k recursion levels.
  * m x n is the plaintext matrix A, n x l the ciphertext matrix Enc(B), w
  * the bit-width of A's entries (1..16) and k the strip width.  Returns
  * PCMM_WS_INVALID for an unknown operation or invalid sizes (so 0 always
@@ -221,6 +222,7 @@ size_t pcmm_cussen_workspace_bytes(int m, int n, int l, int w, int k);
 #define PCMM_OP_NORMALIZE 3
 #define PCMM_OP_CUSSEN_PLAN 4
 #define PCMM_OP_CUSSEN_EXEC 5
+#define PCMM_OP_STRASSEN 6
 #define PCMM_WS_INVALID ((size_t)-1)
 size_t pcmm_workspace_bytes(int op, int m, int n, int l, int w, int k);
 
@@ -307,6 +309,28 @@ pcmm_status pcmm_cussen_execute(const void *plan, int m, int n, int w, int k, co
  * (nothing is launched then), otherwise as pcmm_cussen. */
 pcmm_status pcmm_cussen_static(const uint8_t *A, int m, int n, int w, const uint32_t *ctB, int l,
                                uint32_t *ctC, int k, uint32_t *status, pcmm_stream_t stream);
+
+/* Strassen PC-MM (Section 3.1, the paper's second comparison system):
+ * `levels` steps of 2 x 2 block recursion, each computing seven block
+ * products M1 = (A11 + A22)(B11 + B22), M2 = (A21 + A22) B11,
+ * M3 = A11 (B12 - B22), M4 = A22 (B21 - B11), M5 = (A11 + A12) B22,
+ * M6 = (A21 - A11)(B11 + B12), M7 = (A12 - A22)(B21 + B22) and
+ * C11 = M1 + M4 - M5 + M7, C12 = M3 + M5, C21 = M2 + M4,
+ * C22 = M1 - M2 + M3 + M6 (5 plaintext and 13 ciphertext block additions
+ * per step), with the schoolbook product of the signed block sums at the
+ * leaves.  A, ctB, ctC as pcmm_schoolbook (A uint8, 1 <= w <= 8).
+ * levels: 0..7 with w + levels <= 15 (the block sums of A widen by one bit
+ * per step and are held as int16); m, n and l must be multiples of
+ * 2^levels.  ws: device, 256-byte aligned, at least
+ * pcmm_strassen_workspace_bytes(m, n, l, w, levels) bytes; its first 4 bytes
+ * are a status word (1: an entry of A >= 2^w, masked to w bits), cleared at
+ * the start of every call (pcmm_workspace_status reads it).
+ * Errors: PCMM_EINVAL (null or misaligned pointers, sizes not multiples of
+ * 2^levels, levels or w out of range), PCMM_ENOMEM (workspace too small),
+ * PCMM_EUNSUPPORTED (a launch beyond the grid limits), PCMM_ECUDA. */
+size_t pcmm_strassen_workspace_bytes(int m, int n, int l, int w, int levels);
+pcmm_status pcmm_strassen(const uint8_t *A, int m, int n, int w, const uint32_t *ctB, int l, uint32_t *ctC,
+                          int levels, void *ws, size_t ws_bytes, pcmm_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * Batched PC-MM: many Cussen instances of different shapes and bit-widths

@@ -138,6 +138,57 @@ def schoolbook_counts(A: np.ndarray, l: int) -> dict:
             "add": chains * int(np.maximum(rows_nnz - 1, 0).sum())}
 
 
+def strassen_counts(A: np.ndarray, w: int, levels: int, l: int) -> dict:
+    """Point operations of pcmm_strassen (Section 3.1) for the l output
+    columns, both ciphertext components: per recursion step the ciphertext
+    block sums (five mixed additions per position of a quadrant of Enc(B))
+    and the combination (eight full additions per position of a quadrant of
+    C); at the leaves, per non-zero signed block-sum entry a and output
+    column, the double-and-add of |a| (bitlen - 1 doublings, popcount - 1
+    additions) and one addition into the output after a row's first term.
+    The block sums of A are recomputed here exactly as the kernels form
+    them."""
+    blocks = (np.asarray(A).astype(np.int64) & ((1 << w) - 1))[None]
+    csum = comb = 0
+    for t in range(levels):
+        nodes, mp, np_ = blocks.shape
+        mh, nh, lh = mp // 2, np_ // 2, (l >> t) // 2
+        a11, a12 = blocks[:, :mh, :nh], blocks[:, :mh, nh:]
+        a21, a22 = blocks[:, mh:, :nh], blocks[:, mh:, nh:]
+        blocks = np.stack([a11 + a22, a21 + a22, a11, a22, a11 + a12, a21 - a11, a12 - a22],
+                          axis=1).reshape(nodes * 7, mh, nh)
+        csum += 2 * nodes * 5 * nh * lh
+        comb += 2 * nodes * 8 * mh * lh
+    ld = l >> levels
+    a = np.abs(blocks)
+    nz = a[a != 0]
+    bl = np.zeros(nz.shape, dtype=np.int64)
+    pc = np.zeros(nz.shape, dtype=np.int64)
+    for b in range(16):
+        bit = (nz >> b) & 1
+        pc += bit
+        bl = np.where(bit == 1, b, bl)
+    rows_nnz = (a != 0).sum(axis=2)
+    chains = 2 * ld
+    return {"leaf_dbl": chains * int(bl.sum()), "leaf_madd": chains * int((pc - 1).sum()),
+            "leaf_add": chains * int(np.maximum(rows_nnz - 1, 0).sum()), "block_madd": csum, "block_add": comb}
+
+
+def strassen_point_ops(c: dict) -> int:
+    return c["leaf_dbl"] + c["leaf_madd"] + c["leaf_add"] + c["block_madd"] + c["block_add"]
+
+
+def strassen_equiv(n: int, t: int) -> int:
+    """The paper's equivalent point additions of Strassen PC-MM of square
+    n x n matrices recursed to single entries (Sections 3.1 and 3.3)."""
+    mults, adds, k = 1, 0, 1
+    while k < n:
+        adds = 7 * adds + 13 * k * k
+        mults *= 7
+        k *= 2
+    return 4 * t * mults + 2 * adds
+
+
 def naf4(x: int) -> list:
     """Width-4 non-adjacent form of x >= 0, least significant digit first
     (digits in {0, +-1, +-3, +-5, +-7}): the recoding the decryption kernel's

@@ -306,6 +306,9 @@ extern "C" size_t pcmm_workspace_bytes(int op, int m, int n, int l, int w, int k
         case PCMM_OP_CUSSEN_EXEC:
             b = pcmm_cussen_exec_bytes(m, n, l, w, k ? k : pcmm_cussen_choose_k(m, n, l, w));
             break;
+        case PCMM_OP_STRASSEN:
+            b = pcmm_strassen_workspace_bytes(m, n, l, w, k);
+            break;
         default:
             return PCMM_WS_INVALID;
     }

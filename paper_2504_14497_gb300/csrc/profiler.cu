@@ -22,7 +22,8 @@ int g_used = 0;
 bool g_on = false;
 const char* const g_names[KID_COUNT] = {"plan", "table", "gather", "normalize",
                                         "encrypt", "schoolbook", "comb", "batched", "combine",
-                                        "bsgs", "decrypt"};
+                                        "bsgs", "decrypt", "strassen_sum", "strassen_leaf",
+                                        "strassen_combine"};
 }  // namespace
 
 ProfScope::ProfScope(int kernel_id, cudaStream_t s) : slot(-1), stream(s) {

@@ -17,7 +17,10 @@ enum KernelId {
     KID_COMBINE = 8,
     KID_BSGS = 9,
     KID_DECRYPT = 10,
-    KID_COUNT = 11
+    KID_STRASSEN_SUM = 11,
+    KID_STRASSEN_LEAF = 12,
+    KID_STRASSEN_COMBINE = 13,
+    KID_COUNT = 14
 };
 
 // Records a start event on construction and a stop event on destruction

@@ -203,3 +203,29 @@ def test_static_scratch_holds_the_headline_problem():
     assert 1024 * 2 * L["njb"] >= 12288          # the gather does not split
     one_strip = L["items_per_strip"] * L["item_u4"] * 16 + _a256(L["emax"] * 2 * L["lp"] * 64)
     assert L["plan_bytes"] + one_strip <= 32 << 20
+
+
+def test_strassen_host_validation(lib):
+    # Workspace sizing and argument checks, no GPU (dummy pointers unused).
+    assert pcmm.strassen_workspace_bytes(16, 16, 16, 4, 0) == 256
+    assert pcmm.strassen_workspace_bytes(16, 16, 16, 4, 1) > 256
+    assert pcmm.strassen_workspace_bytes(16, 12, 16, 4, 3) == 0      # 12 not a multiple of 8
+    assert pcmm.strassen_workspace_bytes(16, 16, 16, 8, 8) == 0      # more than 7 levels
+    assert pcmm.strassen_workspace_bytes(256, 256, 256, 8, 7) > 0    # |block sums| <= 2^7 255 fit int16
+    assert pcmm.strassen_workspace_bytes(16, 16, 16, 9, 1) == 0      # uint8 A
+    # Level t holds 7^t blocks: plaintext int16, affine and Jacobian ciphertexts.
+    m, n, l, d = 64, 32, 16, 2
+    want, nodes = 256, 1
+    for t in range(1, d + 1):
+        nodes *= 7
+        for b in (nodes * (m >> t) * (n >> t) * 2, nodes * (n >> t) * (l >> t) * 128,
+                  nodes * (m >> t) * (l >> t) * 192):
+            want = (want + b + 255) // 256 * 256
+    assert pcmm.strassen_workspace_bytes(m, n, l, 4, d) == want
+    assert pcmm.workspace_bytes(pcmm.OP_STRASSEN, m, n, l, 4, d) == want
+    assert pcmm.workspace_bytes(pcmm.OP_STRASSEN, 16, 12, 16, 4, 3) == pcmm.WS_INVALID
+    d8 = ctypes.c_void_p(256)
+    assert lib.pcmm_strassen(None, 16, 16, 4, d8, 16, d8, 1, d8, 1 << 30, None) == 1
+    assert lib.pcmm_strassen(d8, 16, 12, 4, d8, 16, d8, 3, d8, 1 << 30, None) == 1
+    assert lib.pcmm_strassen(d8, 16, 16, 4, d8, 16, d8, 1, ctypes.c_void_p(272), 1 << 30, None) == 1
+    assert lib.pcmm_strassen(d8, 16, 16, 4, d8, 16, d8, 1, d8, 300, None) == 2

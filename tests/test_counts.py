@@ -47,3 +47,26 @@ def test_naf4_recoding():
     # About one non-zero digit in five for random 256-bit scalars.
     nz = np.mean([sum(1 for v in counts.naf4(x) if v) for x in xs[11:]])
     assert 45 < nz < 58
+
+
+def test_strassen_counts():
+    import json
+    import os
+
+    import numpy as np
+
+    from paper_2504_14497_gb300 import counts
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "appendix_counts.json")))
+    for t in gold["t"]:
+        for ni, n in enumerate(gold["n"]):
+            assert counts.strassen_equiv(n, t) == gold["pcmm_equiv"]["strassen"][str(t)][ni]
+    rng = np.random.default_rng(4)
+    A = rng.integers(0, 16, size=(16, 16), dtype=np.uint8)
+    # Depth 0 is the schoolbook product.
+    c0, sb = counts.strassen_counts(A, 4, 0, 16), counts.schoolbook_counts(A, 16)
+    assert (c0["leaf_dbl"], c0["leaf_madd"], c0["leaf_add"]) == (sb["dbl"], sb["madd"], sb["add"])
+    assert c0["block_madd"] == c0["block_add"] == 0
+    # One step: 5 ciphertext sums over 8 x 8 quadrants, 8 output additions
+    # over 8 x 8 quadrants, both components.
+    c1 = counts.strassen_counts(A, 4, 1, 16)
+    assert c1["block_madd"] == 2 * 5 * 64 and c1["block_add"] == 2 * 8 * 64
