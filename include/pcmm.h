@@ -433,7 +433,9 @@ pcmm_status pcmm_copy_columns(uint32_t *dst, size_t dst_ld, size_t dst_col, cons
  * instructions per iteration, so the rate is threads x iters x ops / time.
  * op: PCMM_PEAK_MAD_LO (mad.lo.u32), PCMM_PEAK_MAD_HI (mad.hi.u32),
  * PCMM_PEAK_MAD_WIDE (mad.wide.u32: one 32 x 32 -> 64-bit limb product),
- * PCMM_PEAK_ADD_CARRY (add.cc / addc carry chains), PCMM_PEAK_ADD (add.u32).
+ * PCMM_PEAK_ADD_CARRY (add.cc / addc carry chains), PCMM_PEAK_ADD (add.u32),
+ * PCMM_PEAK_MUL_WIDE (mul.wide.u32 chains: one 32 x 32 -> 64-bit product
+ * each, multiplicand taken from the previous product).
  * sink: device, 1024 words, practically never written.
  * Errors: PCMM_EINVAL (unknown op, blocks or iters < 1, null sink), PCMM_ECUDA.
  * ---------------------------------------------------------------------- */
@@ -442,6 +444,7 @@ pcmm_status pcmm_copy_columns(uint32_t *dst, size_t dst_ld, size_t dst_col, cons
 #define PCMM_PEAK_MAD_WIDE 2
 #define PCMM_PEAK_ADD_CARRY 3
 #define PCMM_PEAK_ADD 4
+#define PCMM_PEAK_MUL_WIDE 5
 int pcmm_peak_ops_per_iter(int op);
 int pcmm_peak_threads_per_block(void);
 pcmm_status pcmm_peak_run(int op, int blocks, int iters, uint32_t *sink, pcmm_stream_t stream);

@@ -48,6 +48,15 @@ __global__ void __launch_bounds__(PEAK_THREADS) peak_kernel(int op, int iters, u
                 asm volatile("{\n\t.reg .b32 lo, hi;\n\tmov.b64 {lo, hi}, %1;\n\t"
                              "mad.wide.u32 %0, lo, %2, %0;\n\t}" : "+l"(d[i]) : "l"(d[i ^ 1]), "r"(b));
         }
+    } else if (op == PCMM_PEAK_MUL_WIDE) {
+        // Each product's multiplicand is the low word of its chain's
+        // previous product: one 32 x 32 -> 64-bit product per instruction.
+        for (int it = 0; it < iters; it++) {
+#pragma unroll
+            for (int i = 0; i < 8; i++)
+                asm volatile("{\n\t.reg .b32 lo, hi;\n\tmov.b64 {lo, hi}, %0;\n\t"
+                             "mul.wide.u32 %0, lo, %1;\n\t}" : "+l"(d[i]) : "r"(b));
+        }
     } else if (op == PCMM_PEAK_ADD_CARRY) {
         // Two independent 4-limb additions with carry per iteration:
         // add.cc, addc.cc, addc.cc, addc (the carry chains of multi-limb
@@ -81,7 +90,7 @@ __global__ void __launch_bounds__(PEAK_THREADS) peak_kernel(int op, int iters, u
 }  // namespace
 
 extern "C" int pcmm_peak_ops_per_iter(int op) {
-    return (op >= PCMM_PEAK_MAD_LO && op <= PCMM_PEAK_ADD) ? 8 : 0;
+    return (op >= PCMM_PEAK_MAD_LO && op <= PCMM_PEAK_MUL_WIDE) ? 8 : 0;
 }
 
 extern "C" int pcmm_peak_threads_per_block(void) { return PEAK_THREADS; }

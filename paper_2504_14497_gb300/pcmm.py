@@ -566,7 +566,7 @@ def normalize(ct_jac, count: int, out=None, stream=None):
 
 # ---------------------------------------------------------- measurement
 
-PEAK_OPS = {"mad_lo": 0, "mad_hi": 1, "mad_wide": 2, "add_carry": 3, "add": 4}
+PEAK_OPS = {"mad_lo": 0, "mad_hi": 1, "mad_wide": 2, "add_carry": 3, "add": 4, "mul_wide": 5}
 
 
 def peak_run(op: str, blocks: int, iters: int, sink, stream=None) -> int:
