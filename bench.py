@@ -384,14 +384,16 @@ def run_ours(args, dist):
         sec = prof[nm][0] / 1e3
         kernels[nm]["products_per_s"] = prods[nm] * args.steps / sec
         kernels[nm]["frac_product_peak"] = kernels[nm]["products_per_s"] / prod_peak
-        rec = recorded_profile(nm)
+        # The records' instruction mix was captured at w in {1, 2, 4, 8}.
+        rec = recorded_profile(nm) if set(widths) <= {1, 2, 4, 8} else None
         if rec and rec.get("alu_warp_inst_per_unit"):
             alu_rate = units[nm] * args.steps * rec["alu_warp_inst_per_unit"] * 32 / sec
             kernels[nm]["alu_inst_per_s"] = alu_rate
             kernels[nm]["frac_alu_peak"] = alu_rate / alu_peak
     dom = max(("gather", "table"), key=lambda nm: prof[nm][0])
     dom_ms, dom_launches = prof[dom]
-    rec = recorded_profile(dom) if (m, n, l) == (1024, 1024, 256) else None
+    # The recorded traffic is per launch of the 1024 x 1024 x 256 step at w in {1, 2, 4, 8}.
+    rec = recorded_profile(dom) if (m, n, l) == (1024, 1024, 256) and sorted(widths) == [1, 2, 4, 8] else None
     roofline = {"bound": "alu", "kernel": dom, "achieved": kernels[dom]["products_per_s"] / 1e12,
                 "peak": prod_peak / 1e12, "unit": "T limb-products/s",
                 "frac": kernels[dom]["frac_product_peak"],
