@@ -491,7 +491,9 @@ def run_ours(args, dist):
 
 def run_batched(args, dist):
     """64 independent PC-MM instances (m, n, l uniform in [32, 768], w uniform
-    in {1..8}, 8-bit messages): strip widths from the autotuner, all instances
+    in {1..8}, 8-bit messages): strip widths and pass sizes from the autotuner
+    (the pass size given to each instance of the persistent launch and to its
+    plain launch; the library's default passes timed as well), all instances
     in one persistent launch replayed from a CUDA graph, against one plain
     pcmm_cussen launch per instance on the same GPU."""
     import torch
@@ -509,8 +511,11 @@ def run_batched(args, dist):
     cache = {}
     items, ops = [], 0
     t_tune = time.perf_counter()
+    strips = []
     for i, (m, n, l, w) in enumerate(shapes):
-        k = autotune.tune(m, n, l, w, device=dev, cache=cache)
+        sched = autotune.tune_schedule(m, n, l, w, device=dev, cache=cache)
+        k = sched["k"]
+        strips.append(sched["strips"])
         A_h = st["A"].integers(0, 1 << w, size=(m, n), dtype=np.uint8)
         msg = st["B"].integers(0, 256, size=(n * l,), dtype=np.uint8)
         r = inputs.uniform_scalars(st["r"], (n * l,))
@@ -519,6 +524,34 @@ def run_batched(args, dist):
         ops += counts.point_ops(counts.cussen_counts(A_h, w, k, l))
     t_tune = time.perf_counter() - t_tune
     torch.cuda.synchronize()
+
+    def persistent_ms(batch_items):
+        """Mean ms of `steps` graph replays of one persistent launch."""
+        b = pcmm.Batch(batch_items)
+        st = torch.cuda.Stream()
+        st.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(st):
+            for _ in range(max(args.warmup, 1)):
+                b.run()
+            torch.cuda.synchronize()
+            gr = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(gr, stream=st):
+                b.run()
+        torch.cuda.synchronize()
+        c = torch.cuda.current_stream()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(c)
+        for _ in range(args.steps):
+            gr.replay()
+        a1.record(c)
+        a1.synchronize()
+        if pcmm.workspace_status(b.ws) != 0:
+            raise RuntimeError("batched run reported a device error")
+        return a0.elapsed_time(a1) / args.steps
+
+    # The library's default pass sizes, for context.
+    ms_default_schedule = persistent_ms(items)
+    items = [it + (S,) for it, S in zip(items, strips)]
     batch = pcmm.Batch(items)
     stream = torch.cuda.Stream()
     stream.wait_stream(torch.cuda.current_stream())
@@ -545,13 +578,15 @@ def run_batched(args, dist):
     # One plain launch per instance (plan + tables + gather each), same k.
     # The launches run one after another on one stream, so they share one
     # allocation; each gets exactly its default workspace size.
-    need = [pcmm.cussen_workspace_bytes(A.shape[0], A.shape[1], l, w, k) for A, _, l, w, k in items]
+    # Each gets the workspace of its tuned pass size (its default when none was better).
+    need = [pcmm.cussen_workspace_bytes_for(A.shape[0], A.shape[1], l, w, k, S) if S
+            else pcmm.cussen_workspace_bytes(A.shape[0], A.shape[1], l, w, k) for A, _, l, w, k, S in items]
     shared = torch.empty(max(need), dtype=torch.uint8, device=dev)
     wss = [shared[:nb] for nb in need]
-    outs = [torch.empty(48 * A.shape[0] * l, dtype=torch.int32, device=dev) for A, _, l, w, k in items]
+    outs = [torch.empty(48 * it[0].shape[0] * it[2], dtype=torch.int32, device=dev) for it in items]
 
     def plain():
-        for (A, ctB, l, w, k), ws, out in zip(items, wss, outs):
+        for (A, ctB, l, w, k, _), ws, out in zip(items, wss, outs):
             pcmm.cussen(A, ctB, l, w, k=k, ws=ws, out=out)
 
     plain()
@@ -563,7 +598,7 @@ def run_batched(args, dist):
     e1.synchronize()
     ms_plain = e0.elapsed_time(e1) / args.steps
     same = all(torch.equal(pcmm.normalize(o, A.shape[0] * l), pcmm.normalize(b, A.shape[0] * l))
-               for o, b, (A, _, l, _, _) in zip(outs, batch.outs, items))
+               for o, b, (A, _, l, _, _, _) in zip(outs, batch.outs, items))
     return {"workload": "batched: 64 PC-MM instances, m,n,l ~ U[32,768], w ~ U{1..8}, 8-bit messages, "
                         "one persistent launch replayed from a CUDA graph",
             "metric": "point-adds/s (batched) vs one launch per instance", "unit": "point-adds/s",
@@ -571,6 +606,8 @@ def run_batched(args, dist):
             "plain_value": ops / (ms_plain / 1e3), "plain_ms_per_batch": ms_plain,
             "speedup_vs_plain": ms_plain / ms_batched, "point_ops_per_batch": ops,
             "outputs_identical": bool(same), "k": [it[4] for it in items],
+            "strips_per_pass": [it[5] for it in items],
+            "ms_per_batch_default_schedule": ms_default_schedule,
             "autotune_s": t_tune, "steps": args.steps, "n_gpus": 1}
 
 

@@ -197,6 +197,12 @@ pcmm_status pcmm_schoolbook16(const uint16_t *A, int m, int n, int w, const uint
  * Accepts 1 <= w <= 16; returns 0 for invalid arguments. */
 int pcmm_cussen_choose_k(int m, int n, int l, int w);
 
+/* Workspace bytes with which pcmm_cussen (or pcmm_cussen16) processes
+ * `strips` strips per pass (the pass size: table warps of a launch, and the
+ * scratch and tables they hold), for strip width k >= 1; 0 for invalid
+ * arguments.  strips is capped at the strips of the matrix. */
+size_t pcmm_cussen_workspace_bytes_for(int m, int n, int l, int w, int k, int strips);
+
 /* Workspace bytes pcmm_cussen (w <= 8) or pcmm_cussen16 (w <= 16) needs for
  * this shape and strip width k (k = 0: the pcmm_cussen_choose_k value).
  * Returns 0 for invalid arguments.  Larger workspaces let a call process
@@ -339,8 +345,10 @@ pcmm_status pcmm_strassen(const uint8_t *A, int m, int n, int w, const uint32_t 
 
 /* One instance: A (device uint8 m x n, entries < 2^w), ctB (device affine
  * ciphertext matrix n x l), ctC (device Jacobian output m x l), strip width
- * k (0: pcmm_cussen_choose_k).  Outputs must not overlap each other or any
- * input. */
+ * k (0: pcmm_cussen_choose_k), strips per pass (0: the library's rule, see
+ * pcmm_batched_workspace_bytes; > 0: that many, capped by the strips of the
+ * instance, by 2 GB per table buffer and by max_strips).  Outputs must not
+ * overlap each other or any input. */
 typedef struct {
     const uint8_t *A;
     int m, n, w;
@@ -348,6 +356,7 @@ typedef struct {
     int l;
     uint32_t *ctC;
     int k;
+    int strips;
 } pcmm_problem;
 
 /* Launch description written by pcmm_batched_prepare (caller-owned POD). */

@@ -1,8 +1,13 @@
-"""Strip-width autotuner for Cussen PC-MM.
+"""Strip-width and pass-size autotuner for Cussen PC-MM.
 
 For a problem shape (m, n, l, w) it times ``pcmm_cussen`` on the device for
 the strip widths around the library's cost-model choice and keeps the
-fastest (the cost model's choice unless another is at least 2% faster).
+fastest (the cost model's choice unless another is at least 2% faster);
+``tune_schedule`` then times, for that width, passes of one to four whole
+waves of table warps and of all strips at once (the tile schedule: how many
+column strips one table launch builds and one gather launch consumes) and
+keeps the fastest (the library's default pass unless another is at least 2%
+faster).
 Inputs are synthetic (uniform w-bit A, random words for the ciphertext
 coordinates): the kernels' work depends on the distinct values of A, not on
 the points.  Results are cached in a JSON file (``PCMM_AUTOTUNE_CACHE``
@@ -16,6 +21,11 @@ import os
 import numpy as np
 
 from . import pcmm
+
+# One wave of the table kernel on a 152-SM GB300: 7 blocks of 4 warps per SM.
+WAVE_ITEMS = 152 * 7 * 4
+# Pass sizes whose workspace would exceed this are not tried.
+SCHEDULE_BYTES_CAP = 24 << 30
 
 def candidates(m: int, n: int, l: int, w: int) -> list:
     kmax = max(1, min(pcmm.PCMM_MAX_WK // w, n))
@@ -89,3 +99,56 @@ def tune(m: int, n: int, l: int, w: int, device="cuda", reps: int = 2, cache=Non
     cache[key] = {"k": int(k_best), "ms": {str(k): t for k, t in times.items()}}
     save_cache(cache, path)
     return int(k_best)
+
+
+def strip_candidates(m: int, n: int, l: int, w: int, k: int) -> list:
+    """Pass sizes (strips per pass) tried for width k: one to four whole
+    waves of table warps, and all strips in one pass, within the byte cap."""
+    nstrips = -(-n // k)
+    items_per_strip = 2 * (-(-l // 32))
+    wave = max(1, WAVE_ITEMS // items_per_strip)
+    cands = {min(nstrips, q * wave) for q in (1, 2, 3, 4)} | {nstrips}
+    return sorted(S for S in cands
+                  if pcmm.cussen_workspace_bytes_for(m, n, l, w, k, S) <= SCHEDULE_BYTES_CAP)
+
+
+def tune_schedule(m: int, n: int, l: int, w: int, device="cuda", reps: int = 2, cache=None, path=None) -> dict:
+    """{"k": strip width, "strips": strips per pass (0: the library's
+    default pass)}, measured and cached with the strip width."""
+    import torch
+
+    key = f"{m},{n},{l},{w}"
+    cache = load_cache(path) if cache is None else cache
+    k = tune(m, n, l, w, device=device, reps=reps, cache=cache, path=path)
+    ent = cache[key]
+    if "strips" in ent:
+        return {"k": k, "strips": int(ent["strips"])}
+    A, ctB = _synthetic(m, n, l, w, device)
+    out = torch.empty(48 * m * l, dtype=torch.int32, device=device)
+
+    def timed(ws):
+        pcmm.cussen(A, ctB, l, w, k=k, ws=ws, out=out)
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            pcmm.cussen(A, ctB, l, w, k=k, ws=ws, out=out)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best
+
+    ws = pcmm.workspace(m, n, l, w, k, device=device)
+    t_default = timed(ws)
+    del ws
+    times = {}
+    for S in strip_candidates(m, n, l, w, k):
+        ws = torch.empty(pcmm.cussen_workspace_bytes_for(m, n, l, w, k, S), dtype=torch.uint8, device=device)
+        times[S] = timed(ws)
+        del ws
+    best = min(times, key=times.get) if times else 0
+    strips = best if times and times[best] < 0.98 * t_default else 0
+    ent["strips"] = int(strips)
+    ent["strips_ms"] = {"default": t_default, **{str(S): t for S, t in times.items()}}
+    save_cache(cache, path)
+    return {"k": k, "strips": int(strips)}

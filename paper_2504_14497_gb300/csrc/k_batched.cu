@@ -197,7 +197,15 @@ struct HostLayout {
 const size_t PASS_ITEMS = PCMM_BATCH_PASS_ITEMS;
 const size_t BUFFER_CAP = (size_t)2 << 30;
 
-int strips_per_pass(const Layout& L, int max_strips) {
+int strips_per_pass(const Layout& L, int max_strips, int strips) {
+    if (strips > 0) {
+        size_t S = (size_t)strips;
+        const size_t per_strip = align256(L.table_points_per_strip * 64);
+        if (S > BUFFER_CAP / per_strip) S = BUFFER_CAP / per_strip;
+        if (max_strips > 0 && S > (size_t)max_strips) S = max_strips;
+        if (S > (size_t)L.nstrips) S = L.nstrips;
+        return S < 1 ? 1 : (int)S;
+    }
     const size_t per_strip = align256(L.table_points_per_strip * 64);
     size_t S = ((size_t)256 << 20) / (2 * per_strip);
     if (S > 64) S = 64;
@@ -218,7 +226,7 @@ pcmm_status build_layout(const pcmm_problem* probs, int count, int max_strips, i
     size_t off = 256;
     for (int i = 0; i < count; i++) {
         const pcmm_problem& p = probs[i];
-        if (!p.A || !p.ctB || !p.ctC || p.w > PCMM_MAX_W) return PCMM_EINVAL;
+        if (!p.A || !p.ctB || !p.ctC || p.w > PCMM_MAX_W || p.strips < 0) return PCMM_EINVAL;
         int k = p.k ? p.k : pcmm_cussen_choose_k(p.m, p.n, p.l, p.w);
         if (!make_layout(Ls[i], p.m, p.n, p.l, p.w, k)) return PCMM_EINVAL;
     }
@@ -235,7 +243,7 @@ pcmm_status build_layout(const pcmm_problem* probs, int count, int max_strips, i
     for (int i = 0; i < count; i++) {
         const Layout& L = Ls[i];
         Inst& I = H.insts[i];
-        I.S = strips_per_pass(L, max_strips);
+        I.S = strips_per_pass(L, max_strips, probs[i].strips);
         I.nchunks = (L.nstrips + I.S - 1) / I.S;
         I.table_points = (size_t)I.S * L.table_points_per_strip;
         tab_off[i] = off;

@@ -281,6 +281,15 @@ pcmm_status cussen_call(const TA* A, int m, int n, int w, const uint32_t* ctB, i
 
 }  // namespace
 
+extern "C" size_t pcmm_cussen_workspace_bytes_for(int m, int n, int l, int w, int k, int strips) {
+    Layout L;
+    if (k < 1 || strips < 1 || !make_layout(L, m, n, l, w, k)) return 0;
+    const size_t S = (size_t)strips < (size_t)L.nstrips ? (size_t)strips : (size_t)L.nstrips;
+    // Room for the gather's partial sums as the default pass sizes them
+    // (exec_space reserves them first, then fits the strips).
+    return L.plan_bytes + partial_bytes(L, gather_parts(L, default_strips(L))) + S * L.per_strip_bytes;
+}
+
 extern "C" size_t pcmm_cussen_workspace_bytes(int m, int n, int l, int w, int k) {
     if (k == 0) k = pcmm_cussen_choose_k(m, n, l, w);
     Layout L;

@@ -30,7 +30,7 @@ EXPORTS = (
     "pcmm_version", "pcmm_status_string", "pcmm_init", "pcmm_keytable_bytes", "pcmm_keytable",
     "pcmm_encrypt_workspace_bytes", "pcmm_encrypt", "pcmm_encrypt_table", "pcmm_base_mul", "pcmm_bsgs_default_baby", "pcmm_bsgs_bytes", "pcmm_bsgs_build",
     "pcmm_decrypt", "pcmm_schoolbook", "pcmm_schoolbook16", "pcmm_cussen_choose_k",
-    "pcmm_workspace_bytes", "pcmm_cussen_workspace_bytes", "pcmm_cussen", "pcmm_cussen16", "pcmm_cussen_plan_bytes", "pcmm_cussen_plan", "pcmm_cussen_exec_bytes",
+    "pcmm_workspace_bytes", "pcmm_cussen_workspace_bytes_for", "pcmm_cussen_workspace_bytes", "pcmm_cussen", "pcmm_cussen16", "pcmm_cussen_plan_bytes", "pcmm_cussen_plan", "pcmm_cussen_exec_bytes",
     "pcmm_cussen_execute", "pcmm_cussen_static", "pcmm_strassen_workspace_bytes", "pcmm_strassen", "pcmm_batched_workspace_bytes", "pcmm_batched_prepare", "pcmm_batched_run",
     "pcmm_cussen_batched",
     "pcmm_workspace_status", "pcmm_copy_columns", "pcmm_normalize", "pcmm_peak_ops_per_iter",
@@ -78,6 +78,7 @@ def lib():
                 "pcmm_cussen_choose_k": ([ci, ci, ci, ci], ci),
                 "pcmm_workspace_bytes": ([ci, ci, ci, ci, ci, ci], sz),
                 "pcmm_cussen_workspace_bytes": ([ci, ci, ci, ci, ci], sz),
+                "pcmm_cussen_workspace_bytes_for": ([ci, ci, ci, ci, ci, ci], sz),
                 "pcmm_cussen": ([vp, ci, ci, ci, vp, ci, vp, ci, vp, sz, vp], ci),
                 "pcmm_cussen16": ([vp, ci, ci, ci, vp, ci, vp, ci, vp, sz, vp], ci),
                 "pcmm_cussen_plan_bytes": ([ci, ci, ci, ci], sz),
@@ -366,6 +367,11 @@ def cussen_workspace_bytes(m: int, n: int, l: int, w: int, k: int = 0) -> int:
     return int(lib().pcmm_cussen_workspace_bytes(m, n, l, w, k))
 
 
+def cussen_workspace_bytes_for(m: int, n: int, l: int, w: int, k: int, strips: int) -> int:
+    """Workspace bytes with which pcmm_cussen processes `strips` strips per pass."""
+    return int(lib().pcmm_cussen_workspace_bytes_for(m, n, l, w, k, strips))
+
+
 def workspace(m: int, n: int, l: int, w: int, k: int = 0, device="cuda"):
     torch = _torch()
     nb = cussen_workspace_bytes(m, n, l, w, k)
@@ -436,7 +442,8 @@ def strassen(A, ctB, l: int, w: int, levels: int, ws=None, out=None, stream=None
 
 class Problem(ctypes.Structure):
     _fields_ = [("A", ctypes.c_void_p), ("m", ctypes.c_int), ("n", ctypes.c_int), ("w", ctypes.c_int),
-                ("ctB", ctypes.c_void_p), ("l", ctypes.c_int), ("ctC", ctypes.c_void_p), ("k", ctypes.c_int)]
+                ("ctB", ctypes.c_void_p), ("l", ctypes.c_int), ("ctC", ctypes.c_void_p), ("k", ctypes.c_int),
+                ("strips", ctypes.c_int)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -450,8 +457,8 @@ class BatchInfo(ctypes.Structure):
 class Batch:
     """A prepared batch of Cussen PC-MM instances (one persistent launch).
 
-    items: list of (A cuda uint8 [m, n], ctB cuda int32, l, w, k); outputs are
-    allocated here (Jacobian, ``self.outs``)."""
+    items: list of (A cuda uint8 [m, n], ctB cuda int32, l, w, k[, strips per
+    pass]); outputs are allocated here (Jacobian, ``self.outs``)."""
 
     def __init__(self, items, max_strips: int = 0, stream=None):
         torch = _torch()
@@ -460,11 +467,13 @@ class Batch:
         n = len(self.items)
         self.probs = (Problem * n)()
         self.outs = []
-        for i, (A, ctB, l, w, k) in enumerate(self.items):
+        for i, it in enumerate(self.items):
+            A, ctB, l, w, k = it[:5]
+            strips = it[5] if len(it) > 5 else 0
             m, nn = A.shape
             out = torch.empty(PCMM_JAC_WORDS * m * l, dtype=torch.int32, device=A.device)
             self.outs.append(out)
-            self.probs[i] = Problem(A.data_ptr(), m, nn, w, ctB.data_ptr(), l, out.data_ptr(), k)
+            self.probs[i] = Problem(A.data_ptr(), m, nn, w, ctB.data_ptr(), l, out.data_ptr(), k, strips)
         self.max_strips = int(max_strips)
         nb = int(L.pcmm_batched_workspace_bytes(ctypes.cast(self.probs, ctypes.c_void_p), n, self.max_strips))
         if nb == 0:
@@ -487,7 +496,7 @@ def problems(items):
         m, n = A.shape
         if A.element_size() != 1:
             raise TypeError("batched problems take a uint8 A")
-        arr[i] = Problem(_ptr(A).value, m, n, w, _ptr(ctB).value, l, _ptr(ctC).value, k)
+        arr[i] = Problem(_ptr(A).value, m, n, w, _ptr(ctB).value, l, _ptr(ctC).value, k, 0)
     return arr
 
 

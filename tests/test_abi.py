@@ -229,3 +229,23 @@ def test_strassen_host_validation(lib):
     assert lib.pcmm_strassen(d8, 16, 12, 4, d8, 16, d8, 3, d8, 1 << 30, None) == 1
     assert lib.pcmm_strassen(d8, 16, 16, 4, d8, 16, d8, 1, ctypes.c_void_p(272), 1 << 30, None) == 1
     assert lib.pcmm_strassen(d8, 16, 16, 4, d8, 16, d8, 1, d8, 300, None) == 2
+
+
+def test_workspace_for_a_pass_size(lib):
+    # plan + S strips of scratch and tables (no partial sums when the gather
+    # does not split), capped at the matrix's strips; the default workspace
+    # is the one for the default pass.
+    from tests.layout_mirror import _a256, layout
+
+    for (m, n, l, w, k) in [(1024, 1024, 256, 8, 1), (1024, 700, 256, 4, 2)]:
+        L = layout(m, n, w, k, l)
+        per_strip = L["items_per_strip"] * L["item_u4"] * 16 + _a256(L["emax"] * 2 * L["lp"] * 64)
+        for S in (1, 7, 100):
+            assert pcmm.cussen_workspace_bytes_for(m, n, l, w, k, S) == L["plan_bytes"] + S * per_strip
+        assert (pcmm.cussen_workspace_bytes_for(m, n, l, w, k, 10 ** 6)
+                == L["plan_bytes"] + L["nstrips"] * per_strip)
+        full = pcmm.cussen_workspace_bytes(m, n, l, w, k)
+        S0 = (full - L["plan_bytes"]) // per_strip
+        assert pcmm.cussen_workspace_bytes_for(m, n, l, w, k, S0) == full
+    assert pcmm.cussen_workspace_bytes_for(16, 16, 16, 4, 0, 3) == 0
+    assert pcmm.cussen_workspace_bytes_for(16, 16, 16, 4, 1, 0) == 0

@@ -106,6 +106,41 @@ def test_autotuner_picks_a_valid_width_and_caches(dev, tmp_path):
     assert autotune.tune(96, 64, 40, 4, device=dev, path=path) == k   # served from the cache
 
 
+def test_pass_sizes_per_instance_and_schedule_tuning(dev, batch_case, tmp_path):
+    # Explicit strips per pass for every instance (several passes each for
+    # the longer ones) give the same outputs as the library's passes; the
+    # schedule tuner returns a valid pass size and caches it.
+    from paper_2504_14497_gb300 import autotune
+
+    items, probs = batch_case
+    ref = pcmm.Batch(items)
+    ref_outs = ref.run()
+    torch.cuda.synchronize()
+    for strips in (1, 3, 5):
+        b = pcmm.Batch([it + (strips,) for it in items])
+        outs = b.run()
+        torch.cuda.synchronize()
+        assert pcmm.workspace_status(b.ws) == 0
+        for o, r, (A, _, l, _, _) in zip(outs, ref_outs, items):
+            assert np.array_equal(_affine(o, A.shape[0] * l), _affine(r, A.shape[0] * l)), strips
+    path = str(tmp_path / "tune.json")
+    sched = autotune.tune_schedule(96, 200, 40, 4, device=dev, path=path)
+    k = sched["k"]
+    assert k in autotune.candidates(96, 200, 40, 4)
+    assert sched["strips"] == 0 or sched["strips"] in autotune.strip_candidates(96, 200, 40, 4, k)
+    assert autotune.load_cache(path)["96,200,40,4"]["strips"] == sched["strips"]
+    assert autotune.tune_schedule(96, 200, 40, 4, device=dev, path=path) == sched
+    # A workspace sized for a pass of S strips runs S strips per pass: the
+    # product is unchanged.
+    pr = inputs.pcmm_problem(3300, 37, 70, 20, 3)
+    A = torch.from_numpy(pr["A"]).to(dev)
+    ctB = encrypt_gpu(dev, pr)
+    want = oracle.closed_form(pr["A"], pr["r"], pr["sk"], pr["B"]).reshape(-1, 2, 16)
+    for S in (1, 9, 70):
+        ws = torch.empty(pcmm.cussen_workspace_bytes_for(37, 70, 20, 3, 1, S), dtype=torch.uint8, device=dev)
+        assert mismatches(_affine(pcmm.cussen(A, ctB, 20, 3, k=1, ws=ws), 37 * 20), want) == 0, S
+
+
 def test_bounded_wait_gives_up_and_reports(dev):
     import time
 
