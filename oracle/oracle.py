@@ -27,7 +27,9 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "p256_oracle.c")
-_LIB = os.path.join(_HERE, "liboracle.so")
+# ORACLE_LIBRARY may name another build of the same source (the test that
+# compiles deliberate mistakes in with -DORC_PLANT=n); it is used as it is.
+_LIB = os.environ.get("ORACLE_LIBRARY") or os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -40,6 +42,8 @@ class OracleError(RuntimeError):
 
 def build(force: bool = False) -> str:
     """Compile the C oracle into ``oracle/liboracle.so`` (gcc, OpenMP)."""
+    if os.environ.get("ORACLE_LIBRARY"):
+        return _LIB
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=gnu11", "-o", tmp, _SRC]

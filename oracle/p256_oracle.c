@@ -38,6 +38,13 @@
 #include <omp.h>
 #endif
 
+/* Test builds only: -DORC_PLANT=n compiles in one deliberate, plausible
+ * mistake (see tests/test_oracle_mutants.py), so that a test can show that
+ * the pins catch it.  The oracle proper is built with ORC_PLANT = 0. */
+#ifndef ORC_PLANT
+#define ORC_PLANT 0
+#endif
+
 typedef unsigned __int128 u128;
 typedef struct { uint64_t w[4]; } u256;
 
@@ -279,7 +286,8 @@ static pt pt_chord(const pt *a, const pt *b, const u256 *dinv) {
     mont_mul(&FP, &lam, &num, dinv);
     mont_mul(&FP, &lam2, &lam, &lam);
     mod_sub(&FP, &x3, &lam2, &a->x);
-    mod_sub(&FP, &x3, &x3, &b->x);           /* x3 = lambda^2 - x1 - x2 */
+    if (ORC_PLANT == 1) mod_add(&FP, &x3, &x3, &b->x);
+    else mod_sub(&FP, &x3, &x3, &b->x);      /* x3 = lambda^2 - x1 - x2 */
     mod_sub(&FP, &t, &a->x, &x3);
     mont_mul(&FP, &y3, &lam, &t);
     mod_sub(&FP, &y3, &y3, &a->y);           /* y3 = lambda (x1 - x3) - y1 */
@@ -292,7 +300,7 @@ static pt pt_add(const pt *a, const pt *b) {
     if (a->inf) return *b;
     if (b->inf) return *a;
     if (u256_cmp(&a->x, &b->x) == 0) {
-        if (u256_cmp(&a->y, &b->y) == 0) return pt_dbl(a);
+        if (u256_cmp(&a->y, &b->y) == 0) return ORC_PLANT == 2 ? pt_inf() : pt_dbl(a);
         return pt_inf();                     /* b = -a */
     }
     u256 den, inv;
@@ -356,7 +364,8 @@ static void ensure_comb(void) {
     if (g_comb_ready) return;
     for (int i = 0; i < 32; i++) {
         COMB_G[i][0] = pt_inf();
-        for (int v = 1; v < 256; v++) COMB_G[i][v] = pt_add(&COMB_G[i][v - 1], &G_POW2[8 * i]);
+        for (int v = 1; v < 256; v++)
+            COMB_G[i][v] = pt_add(&COMB_G[i][v - 1], &G_POW2[ORC_PLANT == 6 && i == 5 ? 8 * i + 1 : 8 * i]);
     }
     g_comb_ready = 1;
 }
@@ -708,8 +717,8 @@ static pt ladder_counted(uint32_t k, int t, const pt *p, orc_counts *cnt) {
     pt r0 = pt_inf(), r1 = *p;
     for (int i = t - 1; i >= 0; i--) {
         int bit = (k >> i) & 1;
-        pt *ra = bit ? &r0 : &r1;   /* receives r0 + r1 */
-        pt *rd = bit ? &r1 : &r0;   /* is doubled */
+        pt *ra = (bit ^ (ORC_PLANT == 7)) ? &r0 : &r1;   /* receives r0 + r1 */
+        pt *rd = (bit ^ (ORC_PLANT == 7)) ? &r1 : &r0;   /* is doubled */
         if (!r0.inf && !r1.inf) cnt->ecsm_add++;
         if (!rd->inf) cnt->ecsm_dbl++;
         pt s = pt_add(&r1, &r0);
@@ -843,7 +852,7 @@ static void cussen_apply(const cussen_plan *pl, const pt *P, int t, pt *out, pt 
     }
     for (int w = N; w >= 1; w--) {
         if (w != N)
-            for (int i = 0; i + 1 < pl->len[w]; i++)
+            for (int i = ORC_PLANT == 3 ? 1 : 0; i + 1 < pl->len[w]; i++)
                 cur[i + 1] = add_counted(&cur[i + 1], &cur[i], &cnt->recon_add);
         /* Un-sort and re-insert duplicates into level w-1. */
         pt *dst = (w == 1) ? out : nxt;
@@ -974,7 +983,8 @@ int orc_closed_form(const uint16_t *A, int m, int n, int l, const uint32_t *r32,
         to_mont(&FQ, &RM[kj], &r);
         to_mont(&FQ, &bm, &b);
         mont_mul(&FQ, &TM[kj], &RM[kj], &skm);           /* r x */
-        mod_add(&FQ, &TM[kj], &TM[kj], &bm);             /* r x + b */
+        if (ORC_PLANT == 4) mod_sub(&FQ, &TM[kj], &TM[kj], &bm);
+        else mod_add(&FQ, &TM[kj], &TM[kj], &bm);        /* r x + b */
     }
     /* Per output: s1 = sum_k a_ik r_kj, s2 = sum_k a_ik (r_kj x + b_kj) mod q.
      * For a plain a < q and a Montgomery-form y R, mont_mul(a, y R) = a y mod
@@ -1127,7 +1137,7 @@ static void strassen_rec(const int32_t *A, int lda, const pt *B, int ldb, pt *C,
             ct_addsub(c21, M2, M4, +1, cnt);
             ct_addsub(t, M1, M2, -1, cnt);
             ct_addsub(t, t, M3, +1, cnt);
-            ct_addsub(c22, t, M6, +1, cnt);
+            ct_addsub(c22, t, M6, ORC_PLANT == 5 ? -1 : +1, cnt);
         }
     free(S);
     free(T);
