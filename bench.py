@@ -59,7 +59,7 @@ def parse():
                          "on square products (the paper's comparison)")
     ap.add_argument("--sweep-n", default="128,256,512,1024,2048")
     ap.add_argument("--strassen-n", default="128,256,512,1024")
-    ap.add_argument("--strassen-widths", default="4,8")
+    ap.add_argument("--strassen-widths", default="4,8,12,16")
     ap.add_argument("--sweep-widths", default="1,2,3,4,5,6,7,8,12,16")
     ap.add_argument("--vector-n", default="8,16,32,64,128,256,512")
     ap.add_argument("--vector-widths", default="4,8,12,16")
@@ -690,7 +690,7 @@ def run_sweep(args, dist):
 
 def run_strassen(args, dist):
     """The paper's comparison systems on the GPU (Sections 3.1 and 4.2):
-    square A n x n (uniform w-bit) times Enc(B) n x n, schoolbook,
+    square A n x n (uniform w-bit; uint16 for w > 8) times Enc(B) n x n, schoolbook,
     Strassen PC-MM at every recursion depth from 1 to the one leaving 16 x 16
     leaf blocks (at most 5), and Cussen (cost-model k), each timed as one
     launch sequence with CUDA events (best of two after a warm-up); the
@@ -732,7 +732,7 @@ def run_strassen(args, dist):
         out2 = torch.empty_like(out)
         for w in (int(x) for x in args.strassen_widths.split(",")):
             A_h = inputs.plaintext_matrix(seed, n, n, w)
-            A = torch.from_numpy(A_h).to(dev)
+            A = _host_plaintext(A_h).to(dev)
             k = pcmm.choose_k(n, n, n, w)
             ws = pcmm.workspace(n, n, n, w, k, device=dev)
             cu = timed(lambda: pcmm.cussen(A, ctB, n, w, k=k, ws=ws, out=out))

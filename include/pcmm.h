@@ -325,9 +325,9 @@ pcmm_status pcmm_cussen_static(const uint8_t *A, int m, int n, int w, const uint
  * C22 = M1 - M2 + M3 + M6 (5 plaintext and 13 ciphertext block additions
  * per step), with the schoolbook product of the signed block sums at the
  * leaves.  A, ctB, ctC as pcmm_schoolbook (A uint8, 1 <= w <= 8).
- * levels: 0..7 with w + levels <= 15 (the block sums of A widen by one bit
- * per step and are held as int16); m, n and l must be multiples of
- * 2^levels.  ws: device, 256-byte aligned, at least
+ * levels: 0..7; m, n and l must be multiples of 2^levels.  The block sums
+ * of A widen by one bit per step and take both signs; they are held as
+ * int16 while w + levels <= 15, else as int32.  ws: device, 256-byte aligned, at least
  * pcmm_strassen_workspace_bytes(m, n, l, w, levels) bytes; its first 4 bytes
  * are a status word (1: an entry of A >= 2^w, masked to w bits), cleared at
  * the start of every call (pcmm_workspace_status reads it).
@@ -337,6 +337,12 @@ pcmm_status pcmm_cussen_static(const uint8_t *A, int m, int n, int w, const uint
 size_t pcmm_strassen_workspace_bytes(int m, int n, int l, int w, int levels);
 pcmm_status pcmm_strassen(const uint8_t *A, int m, int n, int w, const uint32_t *ctB, int l, uint32_t *ctC,
                           int levels, void *ws, size_t ws_bytes, pcmm_stream_t stream);
+
+/* pcmm_strassen for plaintext entries of up to 16 bits (the paper's t = 12
+ * and 16): A is device uint16 m x n with entries < 2^w, 1 <= w <= 16.
+ * Otherwise as pcmm_strassen (same workspace query). */
+pcmm_status pcmm_strassen16(const uint16_t *A, int m, int n, int w, const uint32_t *ctB, int l, uint32_t *ctC,
+                            int levels, void *ws, size_t ws_bytes, pcmm_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * Batched PC-MM: many Cussen instances of different shapes and bit-widths

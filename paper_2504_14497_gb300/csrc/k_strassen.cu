@@ -31,27 +31,28 @@ namespace {
 constexpr int STRASSEN_MAX_LEVELS = 7;
 
 // Plaintext block sums of one recursion step: for every parent node q and
-// position (i, k) of its top-left quadrant, the seven children's entries.
-// Level 0 reads A (uint8, entries masked to w bits, out-of-range entries
-// flagged in the status word); deeper levels read int16.
-template <class TA>
-__global__ void __launch_bounds__(128) strassen_psum_kernel(const TA* __restrict__ P, int mp, int np,
+// position (i, k) of its top-left quadrant, the seven children's entries
+// (TS: int16, or int32 when w + levels > 15).  The top level (TOP) reads A
+// (uint8 or uint16, entries masked to w bits, out-of-range entries flagged
+// in the status word); deeper levels read the parent level's sums.
+template <class TIN, class TS, bool TOP>
+__global__ void __launch_bounds__(128) strassen_psum_kernel(const TIN* __restrict__ P, int mp, int np,
                                                             long long nodes, uint32_t amask,
-                                                            int16_t* __restrict__ S, uint32_t* status) {
+                                                            TS* __restrict__ S, uint32_t* status) {
     const int mh = mp / 2, nh = np / 2;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nodes * mh * nh) return;
     const int k = (int)(t % nh);
     const int i = (int)((t / nh) % mh);
     const long long q = t / ((long long)nh * mh);
-    const TA* b = P + (size_t)q * mp * np;
+    const TIN* b = P + (size_t)q * mp * np;
     int a[4];
     const size_t idx[4] = {(size_t)i * np + k, (size_t)i * np + nh + k, (size_t)(mh + i) * np + k,
                            (size_t)(mh + i) * np + nh + k};
 #pragma unroll
     for (int u = 0; u < 4; u++) {
-        const TA v = b[idx[u]];
-        if (sizeof(TA) == 1) {
+        const TIN v = b[idx[u]];
+        if (TOP) {
             if ((uint32_t)v & ~amask) atomicOr(status, DEV_ERR_A_RANGE);
             a[u] = (int)((uint32_t)v & amask);
         } else {
@@ -60,14 +61,14 @@ __global__ void __launch_bounds__(128) strassen_psum_kernel(const TA* __restrict
     }
     const int a11 = a[0], a12 = a[1], a21 = a[2], a22 = a[3];
     const size_t st = (size_t)mh * nh;
-    int16_t* s = S + (size_t)7 * q * st + (size_t)i * nh + k;
-    s[0 * st] = (int16_t)(a11 + a22);
-    s[1 * st] = (int16_t)(a21 + a22);
-    s[2 * st] = (int16_t)a11;
-    s[3 * st] = (int16_t)a22;
-    s[4 * st] = (int16_t)(a11 + a12);
-    s[5 * st] = (int16_t)(a21 - a11);
-    s[6 * st] = (int16_t)(a12 - a22);
+    TS* s = S + (size_t)7 * q * st + (size_t)i * nh + k;
+    s[0 * st] = (TS)(a11 + a22);
+    s[1 * st] = (TS)(a21 + a22);
+    s[2 * st] = (TS)a11;
+    s[3 * st] = (TS)a22;
+    s[4 * st] = (TS)(a11 + a12);
+    s[5 * st] = (TS)(a21 - a11);
+    s[6 * st] = (TS)(a12 - a22);
 }
 
 // -Q for an affine point (infinity stays (0, 0)).
@@ -137,9 +138,9 @@ __global__ void __launch_bounds__(128) strassen_csum_kernel(const uint4* __restr
 // signed schoolbook product of its plaintext block (md x nd) and ciphertext
 // block (nd x ld_): one warp per (leaf, row i, component c, 32 columns),
 // each term |a| P by double-and-add, negated when a < 0, added by a
-// complete Jacobian addition.  With no recursion (level 0) the plaintext is
-// A itself, masked to w bits.
-template <class TA>
+// complete Jacobian addition.  With no recursion (TOP: level 0) the
+// plaintext is A itself, masked to w bits.
+template <class TA, bool TOP>
 __global__ void __launch_bounds__(128) strassen_leaf_kernel(const TA* __restrict__ S, int md, int nd, int ld_,
                                                             long long leaves, uint32_t amask,
                                                             const uint4* __restrict__ T,
@@ -162,7 +163,7 @@ __global__ void __launch_bounds__(128) strassen_leaf_kernel(const TA* __restrict
     aff P;
     for (int k = 0; k < nd; k++) {
         int a;
-        if (sizeof(TA) == 1) {
+        if (TOP) {
             const uint32_t v = (uint32_t)a_row[k];
             if ((v & ~amask) && lane == 0 && c == 0 && jb == 0) atomicOr(status, DEV_ERR_A_RANGE);
             a = (int)(v & amask);
@@ -224,7 +225,7 @@ __global__ void __launch_bounds__(128) strassen_combine_kernel(const uint4* __re
 inline size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Workspace: a 256-byte header (status word), then per level t = 1..d the
-// plaintext blocks (int16, 7^t x m_t x n_t), the affine ciphertext blocks
+// plaintext blocks (psum_bytes each, 7^t x m_t x n_t), the affine ciphertext blocks
 // (7^t x n_t x l_t, 128 bytes each) and the Jacobian products
 // (7^t x m_t x l_t, 192 bytes each), with m_t = m / 2^t and so on.
 struct StrassenLayout {
@@ -235,10 +236,14 @@ struct StrassenLayout {
     size_t bytes;
 };
 
+// Bytes of one plaintext block-sum entry: the sums of level t are below
+// 2^(w + t) in magnitude, so int16 while w + levels <= 15, else int32.
+inline int psum_bytes(int w, int levels) { return w + levels <= 15 ? 2 : 4; }
+
 bool strassen_layout(StrassenLayout& L, int m, int n, int l, int w, int levels) {
-    if (m < 1 || n < 1 || l < 1 || w < 1 || w > PCMM_MAX_W || levels < 0 || levels > STRASSEN_MAX_LEVELS ||
-        w + levels > 15)
+    if (m < 1 || n < 1 || l < 1 || w < 1 || w > PCMM_MAX_W16 || levels < 0 || levels > STRASSEN_MAX_LEVELS)
         return false;
+    const int pb = psum_bytes(w, levels);
     const int div = 1 << levels;
     if (m % div || n % div || l % div) return false;
     L.d = levels;
@@ -250,7 +255,7 @@ bool strassen_layout(StrassenLayout& L, int m, int n, int l, int w, int levels) 
         L.n[t] = n >> t;
         L.l[t] = l >> t;
         if (t > 0) {
-            L.offP[t] = off; off = a256(off + (size_t)nodes * L.m[t] * L.n[t] * 2);
+            L.offP[t] = off; off = a256(off + (size_t)nodes * L.m[t] * L.n[t] * pb);
             L.offB[t] = off; off = a256(off + (size_t)nodes * L.n[t] * L.l[t] * 128);
             L.offM[t] = off; off = a256(off + (size_t)nodes * L.m[t] * L.l[t] * 192);
         }
@@ -269,34 +274,29 @@ extern "C" size_t pcmm_strassen_workspace_bytes(int m, int n, int l, int w, int 
     return strassen_layout(L, m, n, l, w, levels) ? L.bytes : 0;
 }
 
-extern "C" pcmm_status pcmm_strassen(const uint8_t* A, int m, int n, int w, const uint32_t* ctB, int l,
-                                     uint32_t* ctC, int levels, void* ws, size_t ws_bytes, pcmm_stream_t stream) {
-    if (!A || !ctB || !ctC || !ws || ((uintptr_t)ws & 255u)) return PCMM_EINVAL;
-    StrassenLayout L;
-    if (!strassen_layout(L, m, n, l, w, levels)) return PCMM_EINVAL;
-    if (ws_bytes < L.bytes) return PCMM_ENOMEM;
-    // The largest launch must fit the grid's x dimension.
-    const long long leaf_warps = L.nodes[L.d] * L.m[L.d] * 2 * ((L.l[L.d] + 31) / 32);
-    if ((leaf_warps + 3) / 4 > 0x7fffffffLL || (long long)L.nodes[L.d] * L.m[L.d] * L.l[L.d] * 2 / 128 > 0x7fffffffLL)
-        return PCMM_EUNSUPPORTED;
-    cudaStream_t st = (cudaStream_t)stream;
-    uint8_t* base = (uint8_t*)ws;
+namespace {
+
+// The launches of one call: TA is A's element type, TS the block-sum type.
+template <class TA, class TS>
+pcmm_status strassen_run(const StrassenLayout& L, const TA* A, int w, const uint32_t* ctB, uint32_t* ctC,
+                         uint8_t* base, cudaStream_t st) {
     uint32_t* status = (uint32_t*)base;
-    const uint32_t amask = (1u << w) - 1u;
+    const uint32_t amask = (uint32_t)((1ull << w) - 1u);
     if (cudaMemsetAsync(status, 0, 4, st) != cudaSuccess) return PCMM_ECUDA;
     // Down: block sums level by level.
     for (int t = 0; t < L.d; t++) {
         const long long pn = L.nodes[t];
-        int16_t* S = (int16_t*)(base + L.offP[t + 1]);
+        TS* S = (TS*)(base + L.offP[t + 1]);
         uint4* T = (uint4*)(base + L.offB[t + 1]);
         const uint4* B = t == 0 ? (const uint4*)ctB : (const uint4*)(base + L.offB[t]);
         ProfScope ps(KID_STRASSEN_SUM, st);
         const long long pthreads = pn * (L.m[t] / 2) * (L.n[t] / 2);
         if (t == 0)
-            strassen_psum_kernel<uint8_t><<<blocks_for(pthreads), 128, 0, st>>>(A, L.m[0], L.n[0], pn, amask, S, status);
+            strassen_psum_kernel<TA, TS, true><<<blocks_for(pthreads), 128, 0, st>>>(A, L.m[0], L.n[0], pn, amask,
+                                                                                   S, status);
         else
-            strassen_psum_kernel<int16_t><<<blocks_for(pthreads), 128, 0, st>>>(
-                (const int16_t*)(base + L.offP[t]), L.m[t], L.n[t], pn, amask, S, status);
+            strassen_psum_kernel<TS, TS, false><<<blocks_for(pthreads), 128, 0, st>>>(
+                (const TS*)(base + L.offP[t]), L.m[t], L.n[t], pn, amask, S, status);
         PCMM_CUDA_CHECK_LAUNCH();
         const long long cthreads = pn * (L.n[t] / 2) * (L.l[t] / 2);
         strassen_csum_kernel<<<blocks_for(cthreads), 128, 0, st>>>(B, L.n[t], L.l[t], pn, T);
@@ -305,16 +305,17 @@ extern "C" pcmm_status pcmm_strassen(const uint8_t* A, int m, int n, int w, cons
     // Leaves.
     {
         const int d = L.d;
+        const long long leaf_warps = L.nodes[d] * L.m[d] * 2 * ((L.l[d] + 31) / 32);
         uint4* M = d == 0 ? (uint4*)ctC : (uint4*)(base + L.offM[d]);
         ProfScope ps(KID_STRASSEN_LEAF, st);
         const unsigned blocks = (unsigned)((leaf_warps + 3) / 4);
         if (d == 0)
-            strassen_leaf_kernel<uint8_t><<<blocks, 128, 0, st>>>(A, L.m[0], L.n[0], L.l[0], 1, amask,
-                                                                 (const uint4*)ctB, M, status);
+            strassen_leaf_kernel<TA, true><<<blocks, 128, 0, st>>>(A, L.m[0], L.n[0], L.l[0], 1, amask,
+                                                                   (const uint4*)ctB, M, status);
         else
-            strassen_leaf_kernel<int16_t><<<blocks, 128, 0, st>>>((const int16_t*)(base + L.offP[d]), L.m[d], L.n[d],
-                                                                 L.l[d], L.nodes[d], amask,
-                                                                 (const uint4*)(base + L.offB[d]), M, status);
+            strassen_leaf_kernel<TS, false><<<blocks, 128, 0, st>>>((const TS*)(base + L.offP[d]), L.m[d], L.n[d],
+                                                                    L.l[d], L.nodes[d], amask,
+                                                                    (const uint4*)(base + L.offB[d]), M, status);
         PCMM_CUDA_CHECK_LAUNCH();
     }
     // Up: each level's products from its children's.
@@ -327,4 +328,33 @@ extern "C" pcmm_status pcmm_strassen(const uint8_t* A, int m, int n, int w, cons
         PCMM_CUDA_CHECK_LAUNCH();
     }
     return PCMM_OK;
+}
+
+template <class TA>
+pcmm_status strassen_call(const TA* A, int m, int n, int w, const uint32_t* ctB, int l, uint32_t* ctC, int levels,
+                          void* ws, size_t ws_bytes, pcmm_stream_t stream) {
+    if (!A || !ctB || !ctC || !ws || ((uintptr_t)ws & 255u)) return PCMM_EINVAL;
+    if (w > 8 * (int)sizeof(TA)) return PCMM_EINVAL;
+    StrassenLayout L;
+    if (!strassen_layout(L, m, n, l, w, levels)) return PCMM_EINVAL;
+    if (ws_bytes < L.bytes) return PCMM_ENOMEM;
+    // The largest launches must fit the grid's x dimension.
+    const long long leaf_warps = L.nodes[L.d] * L.m[L.d] * 2 * ((L.l[L.d] + 31) / 32);
+    if ((leaf_warps + 3) / 4 > 0x7fffffffLL || (long long)L.nodes[L.d] * L.m[L.d] * L.l[L.d] * 2 / 128 > 0x7fffffffLL)
+        return PCMM_EUNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (psum_bytes(w, levels) == 2) return strassen_run<TA, int16_t>(L, A, w, ctB, ctC, (uint8_t*)ws, st);
+    return strassen_run<TA, int32_t>(L, A, w, ctB, ctC, (uint8_t*)ws, st);
+}
+
+}  // namespace
+
+extern "C" pcmm_status pcmm_strassen(const uint8_t* A, int m, int n, int w, const uint32_t* ctB, int l,
+                                     uint32_t* ctC, int levels, void* ws, size_t ws_bytes, pcmm_stream_t stream) {
+    return strassen_call(A, m, n, w, ctB, l, ctC, levels, ws, ws_bytes, stream);
+}
+
+extern "C" pcmm_status pcmm_strassen16(const uint16_t* A, int m, int n, int w, const uint32_t* ctB, int l,
+                                       uint32_t* ctC, int levels, void* ws, size_t ws_bytes, pcmm_stream_t stream) {
+    return strassen_call(A, m, n, w, ctB, l, ctC, levels, ws, ws_bytes, stream);
 }

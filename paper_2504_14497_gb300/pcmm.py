@@ -31,7 +31,7 @@ EXPORTS = (
     "pcmm_encrypt_workspace_bytes", "pcmm_encrypt", "pcmm_encrypt_table", "pcmm_base_mul", "pcmm_bsgs_default_baby", "pcmm_bsgs_bytes", "pcmm_bsgs_build",
     "pcmm_decrypt", "pcmm_schoolbook", "pcmm_schoolbook16", "pcmm_cussen_choose_k",
     "pcmm_workspace_bytes", "pcmm_cussen_workspace_bytes_for", "pcmm_cussen_workspace_bytes", "pcmm_cussen", "pcmm_cussen16", "pcmm_cussen_plan_bytes", "pcmm_cussen_plan", "pcmm_cussen_exec_bytes",
-    "pcmm_cussen_execute", "pcmm_cussen_static", "pcmm_strassen_workspace_bytes", "pcmm_strassen", "pcmm_batched_workspace_bytes", "pcmm_batched_prepare", "pcmm_batched_run",
+    "pcmm_cussen_execute", "pcmm_cussen_static", "pcmm_strassen_workspace_bytes", "pcmm_strassen", "pcmm_strassen16", "pcmm_batched_workspace_bytes", "pcmm_batched_prepare", "pcmm_batched_run",
     "pcmm_cussen_batched",
     "pcmm_workspace_status", "pcmm_copy_columns", "pcmm_normalize", "pcmm_peak_ops_per_iter",
     "pcmm_peak_threads_per_block", "pcmm_peak_run", "pcmm_profile_enable",
@@ -88,6 +88,7 @@ def lib():
                 "pcmm_cussen_static": ([vp, ci, ci, ci, vp, ci, vp, ci, vp, vp], ci),
                 "pcmm_strassen_workspace_bytes": ([ci, ci, ci, ci, ci], sz),
                 "pcmm_strassen": ([vp, ci, ci, ci, vp, ci, vp, ci, vp, sz, vp], ci),
+                "pcmm_strassen16": ([vp, ci, ci, ci, vp, ci, vp, ci, vp, sz, vp], ci),
                 "pcmm_workspace_status": ([vp, u32p, vp], ci),
                 "pcmm_batched_workspace_bytes": ([vp, ci, ci], sz),
                 "pcmm_batched_prepare": ([vp, ci, ci, vp, sz, vp, vp], ci),
@@ -423,9 +424,10 @@ def strassen_workspace_bytes(m: int, n: int, l: int, w: int, levels: int) -> int
 
 
 def strassen(A, ctB, l: int, w: int, levels: int, ws=None, out=None, stream=None):
-    """pcmm_strassen: Strassen PC-MM with `levels` recursion steps.  A: cuda
-    uint8[m, n]; ctB: cuda int32[32 * n * l]; returns the Jacobian
-    ciphertext matrix, cuda int32[48 * m * l]."""
+    """pcmm_strassen (uint8 A) or pcmm_strassen16 (16-bit A, see
+    ``plaintext16``): Strassen PC-MM with `levels` recursion steps.  ctB:
+    cuda int32[32 * n * l]; returns the Jacobian ciphertext matrix, cuda
+    int32[48 * m * l]."""
     torch = _torch()
     m, n = A.shape
     if ws is None:
@@ -435,8 +437,9 @@ def strassen(A, ctB, l: int, w: int, levels: int, ws=None, out=None, stream=None
         ws = torch.empty(nb, dtype=torch.uint8, device=A.device)
     if out is None:
         out = torch.empty(PCMM_JAC_WORDS * m * l, dtype=torch.int32, device=A.device)
-    _check(lib().pcmm_strassen(_ptr(A), m, n, w, _ptr(ctB), l, _ptr(out), int(levels), _ptr(ws), ws.numel(),
-                               _stream(stream)), "pcmm_strassen")
+    name = "pcmm_strassen16" if _wide(A) else "pcmm_strassen"
+    _check(getattr(lib(), name)(_ptr(A), m, n, w, _ptr(ctB), l, _ptr(out), int(levels), _ptr(ws), ws.numel(),
+                                _stream(stream)), name)
     return out
 
 

@@ -212,7 +212,15 @@ def test_strassen_host_validation(lib):
     assert pcmm.strassen_workspace_bytes(16, 12, 16, 4, 3) == 0      # 12 not a multiple of 8
     assert pcmm.strassen_workspace_bytes(16, 16, 16, 8, 8) == 0      # more than 7 levels
     assert pcmm.strassen_workspace_bytes(256, 256, 256, 8, 7) > 0    # |block sums| <= 2^7 255 fit int16
-    assert pcmm.strassen_workspace_bytes(16, 16, 16, 9, 1) == 0      # uint8 A
+    assert pcmm.strassen_workspace_bytes(16, 16, 16, 17, 1) == 0     # at most 16-bit entries
+    # int16 block sums while w + levels <= 15, int32 beyond.
+    def a256(x):
+        return (x + 255) // 256 * 256
+    for w, eb in ((14, 2), (16, 4)):
+        assert pcmm.strassen_workspace_bytes(16, 16, 16, w, 1) == \
+            256 + a256(7 * 64 * eb) + a256(7 * 64 * 128) + a256(7 * 64 * 192)
+    assert lib.pcmm_strassen(ctypes.c_void_p(256), 16, 16, 9, ctypes.c_void_p(256), 16, ctypes.c_void_p(256), 1,
+                             ctypes.c_void_p(256), 1 << 30, None) == 1   # uint8 A takes w <= 8
     # Level t holds 7^t blocks: plaintext int16, affine and Jacobian ciphertexts.
     m, n, l, d = 64, 32, 16, 2
     want, nodes = 256, 1

@@ -98,3 +98,21 @@ def test_out_of_range_entries_and_errors(dev):
     with pytest.raises(pcmm.PcmmError) as e:
         pcmm.strassen(A, ctB, l, w, 4, ws=small)          # l = 8 not a multiple of 16
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("w", [12, 16])
+def test_wide_entries_every_depth(dev, w):
+    """pcmm_strassen16 (the paper's t = 12 and 16): every output at depths
+    0..4 of 32 x 32 times Enc(32 x 32); the block sums are int16 while
+    w + depth <= 15 and int32 beyond, so both layouts are exercised."""
+    m = n = l = 32
+    pr = inputs.pcmm_problem(9400 + w, m, n, l, 1)
+    Ah = inputs.plaintext_matrix(9400 + w, m, n, w)
+    A = pcmm.plaintext16(Ah, dev)
+    ctB = encrypt_gpu(dev, pr)
+    want = oracle.closed_form(Ah, pr["r"], pr["sk"], pr["B"]).reshape(-1, 2, 16)
+    for d in range(5):
+        got = run_affine(lambda: pcmm.strassen(A, ctB, l, w, d), m * l)
+        assert mismatches(got, want) == 0, d
+    ora, _ = oracle.strassen(Ah, oracle.encrypt(oracle.keygen(pr["sk"]), pr["B"], pr["r"]), w, 2)
+    assert mismatches(run_affine(lambda: pcmm.strassen(A, ctB, l, w, 2), m * l), ora.reshape(-1, 2, 16)) == 0
