@@ -111,7 +111,9 @@ size_t pcmm_encrypt_workspace_bytes(void);
  * It caches the comb table of H: a call whose workspace already holds the
  * table of the same H (from an earlier pcmm_encrypt on the same stream
  * order) skips the table build.  Do not write to the workspace between such
- * calls, or clear its first 4 bytes to force a rebuild.  count = 0 only
+ * calls, or clear its first 4 bytes to force a rebuild. Calls that may overlap
+ * on the GPU (different streams without an ordering) need separate
+ * workspaces: a call with another key rewrites the table in place.  count = 0 only
  * builds (or keeps) the table.  Requires pcmm_init on the current device.
  * Errors: PCMM_EINVAL (null or misaligned pointers, H not reduced or
  * infinity, no pcmm_init), PCMM_ENOMEM (ws_bytes too small), PCMM_ECUDA. */

@@ -338,10 +338,17 @@ pcmm_status strassen_call(const TA* A, int m, int n, int w, const uint32_t* ctB,
     StrassenLayout L;
     if (!strassen_layout(L, m, n, l, w, levels)) return PCMM_EINVAL;
     if (ws_bytes < L.bytes) return PCMM_ENOMEM;
-    // The largest launches must fit the grid's x dimension.
+    // Every launch must fit the grid's x dimension (128-thread blocks).
+    const long long max_blocks = 0x7fffffffLL;
     const long long leaf_warps = L.nodes[L.d] * L.m[L.d] * 2 * ((L.l[L.d] + 31) / 32);
-    if ((leaf_warps + 3) / 4 > 0x7fffffffLL || (long long)L.nodes[L.d] * L.m[L.d] * L.l[L.d] * 2 / 128 > 0x7fffffffLL)
-        return PCMM_EUNSUPPORTED;
+    if ((leaf_warps + 3) / 4 > max_blocks) return PCMM_EUNSUPPORTED;
+    for (int t = 0; t < L.d; t++) {
+        const long long sums = L.nodes[t] * (L.m[t] / 2) * (L.n[t] / 2);
+        const long long csums = L.nodes[t] * (L.n[t] / 2) * (L.l[t] / 2);
+        const long long combine = L.nodes[t] * L.m[t + 1] * L.l[t + 1] * 2;
+        if ((sums + 127) / 128 > max_blocks || (csums + 127) / 128 > max_blocks || (combine + 127) / 128 > max_blocks)
+            return PCMM_EUNSUPPORTED;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     if (psum_bytes(w, levels) == 2) return strassen_run<TA, int16_t>(L, A, w, ctB, ctC, (uint8_t*)ws, st);
     return strassen_run<TA, int32_t>(L, A, w, ctB, ctC, (uint8_t*)ws, st);
