@@ -14,10 +14,16 @@ namespace cussen {
 
 constexpr int NLEV = PCMM_N_ITER;   // compression iterations N
 
-// Whether the gather's mixed addition inlines its field multiplications
-// (build-time switch; out of line by default).
+// Which field operations the gather's mixed addition and the table build's
+// chain additions inline (build-time switches, see jacz_madd_t).  Measured
+// on GB300 (w in {8, 4}, 1024 x 1024 x 256): gather 109.3 ms per step all out
+// of line, 108.3 with the squarings inlined, 108.2 with a b - c d, 107.4-107.7
+// with both (3), 112.5-127.8 when multiplications are inlined as well.
 #ifndef PCMM_GATHER_INLINE
-#define PCMM_GATHER_INLINE false
+#define PCMM_GATHER_INLINE 3
+#endif
+#ifndef PCMM_TABLE_INLINE
+#define PCMM_TABLE_INLINE 0
 #endif
 constexpr uint16_t NO_RANK = 0xFFFFu;
 constexpr int PLAN_THREADS = 256;
@@ -527,7 +533,7 @@ __device__ __forceinline__ void lp_normalize(const uint4* src, int E, uint4* pre
 }
 
 // Normalises the E entries of a chain kept as (X, Y, ZZ, ZZZ)
-// (jacz_madd_ratio): entry e holds X and Y in quads 0-3 of its 6-quad
+// (jacz_madd_ratio_t): entry e holds X and Y in quads 0-3 of its 6-quad
 // lane-planar slot in src and its ZZZ factor rr3_e in quads 4-5, and its ZZ
 // factor rr2_e is entry e of rat, so ZZ_e = rr2_0 ... rr2_e (likewise ZZZ);
 // zz, zzz are those of the last entry.  One inversion of zz zzz gives both
@@ -586,7 +592,7 @@ __device__ __forceinline__ void lp_normalize_zz(const uint4* src, int E, const u
 // affine addends A (lane-planar, 4 quads per entry), in (X, Y, ZZ, ZZZ):
 // entry e's X, Y and ZZZ factor go to slot e of `slots` (6 quads), its ZZ
 // factor to entry e of rat, as lp_normalize_zz reads them.  acc ends as the
-// last entry; ones and ok as for jacz_madd_ratio.
+// last entry; ones and ok as for jacz_madd_ratio_t.
 static __device__ __noinline__ void lp_affine_chain(const uint4* A, const uint16_t* ptr, int len, uint4* slots,
                                                     uint4* rat, unsigned lane, jacz& acc, bool& ones, bool& ok) {
     aff D;
@@ -596,7 +602,7 @@ static __device__ __noinline__ void lp_affine_chain(const uint4* A, const uint16
     for (int e = 0; e < len; e++) {
         lp_load_aff(D, A, ptr[e], lane);
         fe r2, r3;
-        jacz_madd_ratio(acc, D, r2, r3, ok, e == 0);
+        jacz_madd_ratio_t<PCMM_TABLE_INLINE>(acc, D, r2, r3, ok, e == 0);
         uint4* b = slots + (size_t)e * 6 * 32 + lane;
         b[0] = fe_lo(acc.X);
         b[32] = fe_hi(acc.X);

@@ -169,9 +169,13 @@ __device__ __forceinline__ void jac_from_jacz(jac& R, const jacz& P) {
     R.Z = fmul(P.ZZ, P.ZZZ);
 }
 
-// INL: field multiplications inlined (true) or out of line (false).
-template <bool INL>
+// INL: which field operations are inlined (bit 0 the squarings, bit 1 the
+// fused a b - c d, bit 2 U2 and S2, bit 3 H^3 and the ZZ, ZZZ updates,
+// bit 4 X1 H^2); the rest run out of line.
+template <int INL>
 __device__ __forceinline__ void jacz_madd_t(jacz& P, const aff& Q) {
+    constexpr bool IS = (INL & 1) != 0, IF = (INL & 2) != 0, IU = (INL & 4) != 0, IZ = (INL & 8) != 0,
+                   IX = (INL & 16) != 0;
     if (aff_is_inf(Q)) return;
     if (fe_is_zero(P.ZZ)) {
         P.X = Q.x;
@@ -181,8 +185,8 @@ __device__ __forceinline__ void jacz_madd_t(jacz& P, const aff& Q) {
         return;
     }
     fe t1, t2, t3, t4, x3;
-    t1 = mul_t<INL>(P.ZZ, Q.x);            // U2
-    t2 = mul_t<INL>(P.ZZZ, Q.y);           // S2
+    t1 = mul_t<IU>(P.ZZ, Q.x);            // U2
+    t2 = mul_t<IU>(P.ZZZ, Q.y);           // S2
     fe_sub(t1, t1, P.X);             // H
     fe_sub(t2, t2, P.Y);             // R
     if (fe_is_zero(t1)) {
@@ -196,21 +200,21 @@ __device__ __forceinline__ void jacz_madd_t(jacz& P, const aff& Q) {
         }
         return;
     }
-    t4 = sqr_t<INL>(t1);                   // H^2
-    t3 = mul_t<INL>(t4, t1);               // H^3
-    P.ZZ = mul_t<INL>(P.ZZ, t4);           // ZZ3 = ZZ1 H^2
-    P.ZZZ = mul_t<INL>(P.ZZZ, t3);         // ZZZ3 = ZZZ1 H^3
-    t4 = mul_t<INL>(t4, P.X);              // X1 H^2
+    t4 = sqr_t<IS>(t1);                   // H^2
+    t3 = mul_t<IZ>(t4, t1);               // H^3
+    P.ZZ = mul_t<IZ>(P.ZZ, t4);           // ZZ3 = ZZ1 H^2
+    P.ZZZ = mul_t<IZ>(P.ZZZ, t3);         // ZZZ3 = ZZZ1 H^3
+    t4 = mul_t<IX>(t4, P.X);              // X1 H^2
     fe_add(t1, t4, t4);              // 2 X1 H^2
-    x3 = sqr_t<INL>(t2);                   // R^2
+    x3 = sqr_t<IS>(t2);                   // R^2
     fe_sub(x3, x3, t1);
     fe_sub(x3, x3, t3);              // X3 = R^2 - 2 X1 H^2 - H^3
     fe_sub(t4, t4, x3);              // X1 H^2 - X3
-    P.Y = mulsub_t<INL>(t4, t2, t3, P.Y);  // Y3 = R (X1 H^2 - X3) - Y1 H^3
+    P.Y = mulsub_t<IF>(t4, t2, t3, P.Y);  // Y3 = R (X1 H^2 - X3) - Y1 H^3
     P.X = x3;
 }
 
-__device__ __forceinline__ void jacz_madd(jacz& P, const aff& Q) { jacz_madd_t<false>(P, Q); }
+__device__ __forceinline__ void jacz_madd(jacz& P, const aff& Q) { jacz_madd_t<0>(P, Q); }
 
 // Doubling in (X, Y, ZZ, ZZZ) coordinates (dbl-2001-b with delta = ZZ): Z
 // would become 2 Y Z, so ZZ is multiplied by rr2 = 4 Y^2 and ZZZ by
@@ -252,7 +256,10 @@ __device__ __forceinline__ void jacz_dbl_ratio(jacz& P, fe& rr2, fe& rr3) {
 // Q is infinity; for the first step, from infinity, ZZ = ZZZ = 1 and the
 // factors are 1).  ok is cleared when no such factors exist (infinity
 // after the first step, or a result at infinity).
-__device__ __forceinline__ void jacz_madd_ratio(jacz& P, const aff& Q, fe& rr2, fe& rr3, bool& ok, bool first) {
+// INL as for jacz_madd_t (bit 0 squarings, bit 1 the fused a b - c d).
+template <int INL>
+__device__ __forceinline__ void jacz_madd_ratio_t(jacz& P, const aff& Q, fe& rr2, fe& rr3, bool& ok, bool first) {
+    constexpr bool IS = (INL & 1) != 0, IF = (INL & 2) != 0;
     fe_one(rr2);
     fe_one(rr3);
     if (aff_is_inf(Q)) {
@@ -282,7 +289,7 @@ __device__ __forceinline__ void jacz_madd_ratio(jacz& P, const aff& Q, fe& rr2, 
         }
         return;
     }
-    t4 = fsqr(t1);                   // H^2
+    t4 = sqr_t<IS>(t1);              // H^2
     t3 = fmul(t4, t1);               // H^3
     rr2 = t4;
     rr3 = t3;
@@ -290,11 +297,11 @@ __device__ __forceinline__ void jacz_madd_ratio(jacz& P, const aff& Q, fe& rr2, 
     P.ZZZ = fmul(P.ZZZ, t3);
     t4 = fmul(t4, P.X);              // X1 H^2
     fe_add(t1, t4, t4);              // 2 X1 H^2
-    x3 = fsqr(t2);                   // R^2
+    x3 = sqr_t<IS>(t2);              // R^2
     fe_sub(x3, x3, t1);
     fe_sub(x3, x3, t3);              // X3 = R^2 - 2 X1 H^2 - H^3
     fe_sub(t4, t4, x3);              // X1 H^2 - X3
-    P.Y = fmulsub(t4, t2, t3, P.Y);  // Y3 = R (X1 H^2 - X3) - Y1 H^3
+    P.Y = mulsub_t<IF>(t4, t2, t3, P.Y);  // Y3 = R (X1 H^2 - X3) - Y1 H^3
     P.X = x3;
 }
 
