@@ -116,3 +116,15 @@ def test_wide_entries_every_depth(dev, w):
         assert mismatches(got, want) == 0, d
     ora, _ = oracle.strassen(Ah, oracle.encrypt(oracle.keygen(pr["sk"]), pr["B"], pr["r"]), w, 2)
     assert mismatches(run_affine(lambda: pcmm.strassen(A, ctB, l, w, 2), m * l), ora.reshape(-1, 2, 16)) == 0
+
+
+def test_deepest_recursion_to_single_entries(dev):
+    """Depth 7 on 128 x 128 times Enc(128 x 128): recursion down to 1 x 1
+    blocks (823,543 leaves, as in the paper's count model), every one of the
+    16,384 outputs against the closed form; w = 8 at depth 7 is the widest
+    int16 case (|block sums| <= 2^7 255)."""
+    m = n = l = 128
+    for w in (1, 8):
+        pr, A, ctB = _problem(dev, 9500 + w, m, n, l, w)
+        got = run_affine(lambda: pcmm.strassen(A, ctB, l, w, 7), m * l)
+        assert mismatches(got, _want(pr)) == 0, w
