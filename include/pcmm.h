@@ -114,7 +114,8 @@ size_t pcmm_encrypt_workspace_bytes(void);
  * calls, or clear its first 4 bytes to force a rebuild. Calls that may overlap
  * on the GPU (different streams without an ordering) need separate
  * workspaces: a call with another key rewrites the table in place.  count = 0 only
- * builds (or keeps) the table.  Requires pcmm_init on the current device.
+ * builds (or keeps) the table; msg, r and ct may then be NULL.  Requires
+ * pcmm_init on the current device.
  * Errors: PCMM_EINVAL (null or misaligned pointers, H not reduced or
  * infinity, no pcmm_init), PCMM_ENOMEM (ws_bytes too small), PCMM_ECUDA. */
 pcmm_status pcmm_encrypt(const uint32_t *H_host, const uint8_t *msg, const uint32_t *r, size_t count,

@@ -413,7 +413,7 @@ extern "C" pcmm_status pcmm_encrypt(const uint32_t* H_host, const uint8_t* msg, 
                                     uint32_t* ct, void* ws, size_t ws_bytes, pcmm_stream_t stream) {
     aff H;
     if (key_from_host(H_host, H) != PCMM_OK) return PCMM_EINVAL;
-    if (!msg || !r || !ct || !ws || ((uintptr_t)ws & 255u)) return PCMM_EINVAL;
+    if ((count && (!msg || !r || !ct)) || !ws || ((uintptr_t)ws & 255u)) return PCMM_EINVAL;
     if (ws_bytes < pcmm_encrypt_workspace_bytes()) return PCMM_ENOMEM;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return PCMM_ECUDA;

@@ -187,6 +187,7 @@ def test_encrypt_and_batched_host_validation(lib):
     Hbig = (ctypes.c_uint32 * 16)(*([0xFFFFFFFF] * 16))                                # not reduced
     assert lib.pcmm_encrypt(Hbig, d, d, 4, d, d, nb, None) == 1
     assert lib.pcmm_encrypt(H, None, d, 4, d, d, nb, None) == 1
+    assert lib.pcmm_encrypt(H, None, None, 0, None, None, nb, None) == 1              # no workspace
     assert lib.pcmm_encrypt(H, d, d, 4, d, ctypes.c_void_p(272), nb, None) == 1       # misaligned ws
     assert lib.pcmm_encrypt(H, d, d, 4, d, d, nb - 1, None) == 2
     assert lib.pcmm_encrypt_table(None, d, d, 4, d, None) == 1

@@ -41,6 +41,16 @@ def test_encrypt_with_host_key_and_cached_table(dev):
         got = _ct_host(pcmm.encrypt(keys[idx], dmsg, dr, ws=ws), count)
         want = oracle.encrypt(keys[idx], msg, r)
         assert mismatches(got, want) == 0, f"call {call} (key {idx})"
+    # count = 0 only builds the table of key 1 (null buffers allowed); the
+    # next call with that key encrypts from it.
+    import ctypes
+    H1 = np.ascontiguousarray(keys[1], dtype=np.uint32)
+    rc = pcmm.lib().pcmm_encrypt(H1.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), None, None, 0, None,
+                                 ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                 ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0
+    assert mismatches(_ct_host(pcmm.encrypt(keys[1], dmsg, dr, ws=ws), count),
+                      oracle.encrypt(keys[1], msg, r)) == 0
     tab = pcmm.keytable(keys[0], device=dev)
     assert mismatches(_ct_host(pcmm.encrypt_table(tab, dmsg, dr), count), want) == 0
     # Clearing the tag forces a rebuild, so a workspace overwritten by other
