@@ -43,11 +43,10 @@ def test_headline_product_every_output(dev, w, k):
     assert mismatches(got, want) == 0
 
 
-def test_batched_workload_every_output_of_ten_instances(dev):
+def test_batched_workload_every_output_of_every_instance(dev):
     """The 64-instance batched workload (m, n, l uniform in [32, 768], w in
-    1..8, cost-model k) in one persistent launch; every output of its eight
-    smallest and two largest instances (by m n l) against the closed form:
-    1,277,355 output ciphertexts."""
+    1..8, cost-model k) in one persistent launch; every output of every
+    instance against the closed form: 9,816,999 output ciphertexts."""
     shapes = inputs.batched_shapes(inputs.SEED_BASE + 4, count=64)
     items, probs = [], []
     for i, (m, n, l, w) in enumerate(shapes):
@@ -58,17 +57,30 @@ def test_batched_workload_every_output_of_ten_instances(dev):
     outs = b.run()
     torch.cuda.synchronize()
     assert pcmm.workspace_status(b.ws) == 0
-    order = sorted(range(len(shapes)), key=lambda i: shapes[i][0] * shapes[i][1] * shapes[i][2])
-    picked = order[:8] + order[-2:]
     compared = 0
-    for i in picked:
-        m, n, l, w = shapes[i]
-        pr = probs[i]
-        got = _affine_host(outs[i], m * l)
+    for (m, n, l, w), pr, out in zip(shapes, probs, outs):
+        got = _affine_host(out, m * l)
         want = oracle.closed_form(pr["A"], pr["r"], pr["sk"], pr["B"]).reshape(m * l, 2, 16)
         assert mismatches(got, want) == 0, (m, n, l, w)
         compared += m * l
-    assert compared == 1277355
+    assert compared == 9816999
+
+
+def test_sweep_point_every_output(dev):
+    """One square sweep point in full: 512 x 512 times Enc(512 x 512), w = 5
+    (cost-model k = 1, one pass), all 262,144 outputs against the closed form."""
+    n, w = 512, 5
+    seed = inputs.SEED_BASE + 3
+    pr = inputs.pcmm_problem(seed, n, n, n, 1)
+    Ah = inputs.plaintext_matrix(seed, n, n, w)
+    ctB = encrypt_gpu(dev, pr)
+    A = torch.from_numpy(Ah).to(dev)
+    k = pcmm.choose_k(n, n, n, w)
+    ws = pcmm.workspace(n, n, n, w, k, device=dev)
+    got = _affine_host(pcmm.cussen(A, ctB, n, w, k=k, ws=ws), n * n)
+    assert pcmm.workspace_status(ws) == 0
+    want = oracle.closed_form(Ah, pr["r"], pr["sk"], pr["B"]).reshape(n * n, 2, 16)
+    assert mismatches(got, want) == 0
 
 
 def _lines(n, extra=()):
