@@ -27,15 +27,16 @@ def _affine_host(jac, count):
     return pcmm.planar_to_ct(pcmm.to_host_words(aff), count)
 
 
-@pytest.mark.parametrize("w,k", [(8, 1), (4, 2)])
+@pytest.mark.parametrize("w,k", [(8, 1), (4, 2), (16, 1)])
 def test_headline_product_every_output(dev, w, k):
     """1024 x 1024 times Enc(1024 x 256) in the benchmark's configuration
-    (default workspace: two passes of strips at w = 8, k = 1): all
-    262,144 output ciphertexts (524,288 points) against the closed form."""
+    (default workspace: two passes of strips at w = 8, k = 1; one wave per
+    pass at the paper's w = 16): all 262,144 output ciphertexts (524,288
+    points) against the closed form."""
     m, n, l = 1024, 1024, 256
     pr = inputs.pcmm_problem(inputs.SEED_BASE + 2, m, n, l, w)
     ctB = encrypt_gpu(dev, pr)
-    A = torch.from_numpy(pr["A"]).to(dev)
+    A = pcmm.plaintext16(pr["A"], dev) if w > 8 else torch.from_numpy(pr["A"]).to(dev)
     ws = pcmm.workspace(m, n, l, w, k, device=dev)
     got = _affine_host(pcmm.cussen(A, ctB, l, w, k=k, ws=ws), m * l)
     assert pcmm.workspace_status(ws) == 0
