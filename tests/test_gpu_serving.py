@@ -1,6 +1,8 @@
 """The continuous-batching server on the GPU: each request's result is
 bit-identical whether it runs alone or packed with others in a mix of
-models, widths and overlapping arrivals, and matches the CPU oracle."""
+models, widths and overlapping arrivals, and every output of every request
+matches the CPU oracle (small models, and the serving workload's MLP
+shapes 256 x 784, 128 x 256 and 10 x 128 with 4-bit weights)."""
 import numpy as np
 import pytest
 
@@ -43,9 +45,40 @@ def test_results_identical_alone_and_in_the_mix():
         alone = pcmm.normalize(plan.execute(req.ct, req.l), info.m * req.l)
         torch.cuda.synchronize()
         assert torch.equal(alone, req.out), req.rid
-    # Spot-check against the oracle's closed form.
-    for req, (msg, r) in list(zip(reqs, plain))[:6]:
+    # Every request against the oracle's closed form.
+    for req, (msg, r) in zip(reqs, plain):
         A = models[req.model][0]
         want = oracle.closed_form(A, r, sk, msg).reshape(-1, 2, 16)
         got = pcmm.planar_to_ct(pcmm.to_host_words(req.out), A.shape[0] * req.l)
         assert np.array_equal(got, want)
+
+
+def test_mlp_shapes_every_output():
+    be = GpuBackend("cuda:0", max_inflight=8)
+    dev = be.device
+    rng = np.random.default_rng(12)
+    shapes = {"mlp_784": (256, 784), "mlp_256": (128, 256), "mlp_out": (10, 128)}
+    models = {nm: (rng.integers(0, 16, size=sh, dtype=np.uint8), 4, 0) for nm, sh in shapes.items()}
+    srv = Server(be, models, hbm_budget=40e9, max_inflight=8, max_batch_cols=256)
+    s = inputs.streams(78)
+    sk = inputs.uniform_scalars(s["sk"], (1,))[0]
+    H = pcmm.public_key(sk, device=dev)
+    reqs, plain = [], []
+    for i in range(12):
+        nm = list(shapes)[i % 3]
+        n = shapes[nm][1]
+        l = int(rng.integers(1, 65))
+        msg = s["B"].integers(0, 256, size=(n, l), dtype=np.uint8)
+        r = inputs.uniform_scalars(s["r"], (n, l))
+        ct = pcmm.encrypt(H, torch.from_numpy(msg.reshape(-1)).to(dev),
+                          pcmm.to_device_words(pcmm.scalars_to_planar(r), dev))
+        reqs.append(Request(i, nm, ct, l, arrival=0.0002 * i))
+        plain.append((msg, r))
+    torch.cuda.synchronize()
+    srv.run(reqs)
+    assert len(srv.completed) == 12 and not srv.rejected
+    for req, (msg, r) in zip(reqs, plain):
+        A = models[req.model][0]
+        want = oracle.closed_form(A, r, sk, msg).reshape(-1, 2, 16)
+        got = pcmm.planar_to_ct(pcmm.to_host_words(req.out), A.shape[0] * req.l)
+        assert np.array_equal(got, want), req.rid
