@@ -58,3 +58,53 @@ def test_strip_tables_match_the_oracle(dev, w, k):
                     idx = ((s * L["emax"] + e) * 2 + c) * L["lp"] + j
                     got = np.concatenate([words[q, idx] for q in range(4)])
                     assert np.array_equal(got, want), (s, e, c, j)
+
+
+@pytest.mark.parametrize("w,k", [(8, 1), (4, 2), (2, 3), (12, 1)])
+def test_every_strip_table_entry(dev, w, k):
+    """Every entry of every strip table (all distinct codes u, both
+    components, all l columns) against the closed form of the entry:
+    component 1 is (sum_t u_t r_t) G and component 2 (sum_t u_t (r_t x +
+    b_t)) G, since B = (r G, r H + b G) with H = x G."""
+    Q = 0xFFFFFFFF00000000FFFFFFFFFFFFFFFFBCE6FAADA7179E84F3B9CAC2FC632551
+    m, n, l = 3072, 2 * k + 1, 64
+    pr = inputs.pcmm_problem(4100 + w, m, n, l, w)
+    A_h = pr["A"]
+    A = pcmm.plaintext16(A_h, dev) if w > 8 else torch.from_numpy(A_h).to(dev)
+    ctB = encrypt_gpu(dev, pr)
+    L = layout(m, n, w, k, l)
+    ws = pcmm.workspace(m, n, l, w, k, device=dev)
+    pcmm.cussen(A, ctB, l, w, k=k, ws=ws)
+    torch.cuda.synchronize()
+    assert pcmm.workspace_status(ws) == 0
+    buf = ws.cpu().numpy()
+    toff, tpoints = single_pass_table(L)
+    words = np.frombuffer(buf[toff:toff + tpoints * 64].tobytes(), dtype=np.uint32).reshape(4, tpoints, 4)
+    sk = oracle.words_to_int(pr["sk"])
+    R = [[oracle.words_to_int(pr["r"][c, j]) for j in range(l)] for c in range(n)]
+    Bm = pr["B"].astype(np.int64)
+    A64 = A_h.astype(np.int64)
+    mask = (1 << w) - 1
+    checked = 0
+    for s in range(L["nstrips"]):
+        cols = list(range(s * k, min(s * k + k, n)))
+        codes = np.zeros(m, dtype=np.int64)
+        for t, c in enumerate(cols):
+            codes |= A64[:, c] << (w * t)
+        distinct = [int(u) for u in np.unique(codes[codes != 0])]
+        scal, idx = [], []
+        for e, u in enumerate(distinct):
+            parts = [((u >> (w * t)) & mask, col) for t, col in enumerate(cols)]
+            for j in range(l):
+                s1 = sum(ut * R[col][j] for ut, col in parts) % Q
+                s2 = sum(ut * (R[col][j] * sk + int(Bm[col, j])) for ut, col in parts) % Q
+                for c, sc in ((0, s1), (1, s2)):
+                    scal.append(sc)
+                    idx.append(((s * L["emax"] + e) * 2 + c) * L["lp"] + j)
+        sw = np.frombuffer(b"".join(int(x).to_bytes(32, "little") for x in scal), dtype="<u4").reshape(-1, 8)
+        want = oracle.base_mul_comb(sw)
+        idx = np.asarray(idx)
+        got = np.concatenate([words[q, idx] for q in range(4)], axis=1)
+        assert np.array_equal(got, want), s
+        checked += len(idx)
+    assert checked > 0
