@@ -671,7 +671,7 @@ int orc_decrypt(const uint32_t *sk32, const uint32_t *ct, size_t count, int64_t 
                 }
                 h = (h + 1) & (cap - 1);
             }
-            M = pt_add(&M, &neg_sg);
+            M = ORC_PLANT == 11 ? pt_add(&M, &sg) : pt_add(&M, &neg_sg);
         }
         out[i] = (found >= 0 && found <= mmax) ? found : -1;
     }
@@ -832,7 +832,7 @@ static int plan_build(cussen_plan *pl, const int32_t *a, int n0, int N) {
         }
         /* Differences of consecutive elements except in the last iteration. */
         if (w != N)
-            for (int i = d - 1; i >= 1; i--) sorted[i] = sorted[i] - sorted[i - 1];
+            for (int i = d - 1; i >= (ORC_PLANT == 9 ? 2 : 1); i--) sorted[i] = sorted[i] - sorted[i - 1];
         pl->lev[w] = sorted;
         pl->len[w] = d;
     }
@@ -856,7 +856,8 @@ static void cussen_apply(const cussen_plan *pl, const pt *P, int t, pt *out, pt 
                 cur[i + 1] = add_counted(&cur[i + 1], &cur[i], &cnt->recon_add);
         /* Un-sort and re-insert duplicates into level w-1. */
         pt *dst = (w == 1) ? out : nxt;
-        for (int i = 0; i < pl->len[w - 1]; i++) dst[i] = cur[pl->ptr[w][i]];
+        for (int i = 0; i < pl->len[w - 1]; i++)
+            dst[i] = cur[(ORC_PLANT == 8 && w == 1 && i == 0) ? pl->len[w] - 1 : pl->ptr[w][i]];
         if (w != 1) { pt *tmp = cur; cur = nxt; nxt = tmp; }
     }
 }
@@ -929,7 +930,7 @@ int orc_cussen(const uint16_t *A, int m, int n, int l, int w, int kstrip, int N,
                                 int e = tp.ptr[1][i];
                                 if (done[e]) continue;
                                 done[e] = 1;
-                                for (int t = 0; t < kw; t++)
+                                for (int t = 0; t < kw - (ORC_PLANT == 10); t++)
                                     tup[e] = add_counted(&tup[e], &colmul[(size_t)t * m + i], &cnt.recon_add);
                             }
                             free(done);

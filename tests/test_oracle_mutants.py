@@ -5,8 +5,10 @@ them to fail.  The unplanted oracle passes the same pins in the rest of the
 CPU suite.  Mistakes: a wrong sign in the chord formula, a missing doubling
 case, a reconstruction prefix sum that skips its first term, a wrong sign
 in the closed form, a wrong sign in a Strassen quadrant combination, a comb
-window built from the wrong power of two, and the ladder's two registers
-swapped."""
+window built from the wrong power of two, the ladder's two registers
+swapped, a wrong tracking pointer in the un-sort step, a skipped difference
+in the compression, k-tuple entries missing a column, and decryption's
+giant step of the wrong sign."""
 import os
 import subprocess
 import sys
@@ -24,6 +26,10 @@ PLANTS = {
     5: ("Strassen C22 = M1 - M2 + M3 - M6", "tests/test_oracle_strassen.py"),
     6: ("comb window 5 built from 2^41 G", "tests/test_oracle_curve.py"),
     7: ("ladder registers swapped", "tests/test_oracle_pcmm.py"),
+    8: ("un-sort takes the wrong entry for the first row", "tests/test_oracle_pcmm.py"),
+    9: ("compression skips the first difference", "tests/test_oracle_pcmm.py"),
+    10: ("k-tuple entries drop their last column", "tests/test_oracle_pcmm.py"),
+    11: ("decryption's giant step adds instead of subtracting", "tests/test_oracle_elgamal.py"),
 }
 
 
